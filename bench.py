@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the SDPD-DEM per-timestep interaction step on GB300.
+
+Workload: single-particle sedimentation, 32 x 32 x 64 fluid lattice
+(65,535 fluid + 1 DEM sphere, d = 4 dx, rho_s = 2500) with 4-layer
+dummy-particle walls in z (8,192 wall particles), dx = 1 mm, h = 3.9 dx,
+dt = 1e-5 s; synthetic seeded inputs.  A step is one full velocity-Verlet step
+(both sub-steps: neighbour build, density, drag, forces, integration,
+artificial viscosity).
+
+Metric: SDPD-DEM pair updates/s = unordered pairs within h evaluated by the
+force pass x 2 evaluations per step x steps / time; also timesteps/s.  The
+headline runs the FP64 path; the split-precision path (FP32 pair arithmetic,
+FP64 state) is measured beside it on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload (the
+instances are independent; no collective on the data path), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SDPD-DEM pair updates/s & timesteps/s on 1 GB300, vs plain FP64 GPU path"
+UNIT = "pair updates/s"
+WORKLOAD = "single-particle sedimentation 32x32x64 (65,535 fluid + 1 sphere + 8,192 wall)"
+# algorithmic FP64 flops per ordered fluid pair evaluation of the force pass
+# (Eqs. FijC, FijD, FijR, FijT incl. Box-Muller; transcendentals counted as 1)
+FLOPS_PER_PAIR = 160.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_case():
+    from paper_2002_03120_gb300 import cases
+    return cases.sedimentation()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ native
+def time_native(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_03120_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    case = make_case()
+    prec = B.SDPD_PREC_FP64 if args.precision == "fp64" else B.SDPD_PREC_SPLIT
+
+    def run_path(precision):
+        sim = B.Sim(case, precision=precision)
+        sim.build_cells(stream)
+        torch.cuda.synchronize()
+        pairs = sim.count_pairs()
+        with torch.cuda.stream(stream):
+            sim.step(args.warmup, stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = []
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                sim.step(1, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        total_ms = float(sum(ms))
+        kernels = sim.graph_kernels()
+        # dominant kernel (force pass, velver 1) timed alone on the stream it
+        # is launched on, L2 flushed before each launch
+        fms = []
+        for _ in range(5):
+            sim.evaluate(1, stream)  # build, density, drag for the current state
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.compute_forces(1, stream)
+            b.record(stream)
+            b.synchronize()
+            fms.append(a.elapsed_time(b))
+        # end-to-end through the C ABI with host buffers: upload the step's
+        # state from pinned memory, run the step, read the result back
+        N = sim.N
+        hx = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
+        hv = torch.empty_like(hx)
+        hw = torch.empty_like(hx)
+        sim.download_state(hx, hv, hw, stream=stream)
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(max(3, args.steps // 2)):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.upload_state(hx, hv, hw, stream=stream)
+            sim.step(1, stream)
+            sim.download_state(hx, hv, hw, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        out = dict(pairs=pairs, ms=total_ms, per_step=ms, kernels=kernels,
+                   force_ms=float(np.median(fms)), e2e_ms=float(np.mean(e2e_ms)),
+                   e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N)
+        sim.close()
+        return out
+
+    main = run_path(prec)
+    other = run_path(B.SDPD_PREC_SPLIT if prec == B.SDPD_PREC_FP64 else B.SDPD_PREC_FP64)
+    return main, other
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 oracle timed on this host's cores on a bounded sample of the
+    workload: full steps of a 16x16x32 sedimentation box (1/8 of the lattice,
+    same physics), until `seconds` of CPU time have elapsed."""
+    import oracle
+    from paper_2002_03120_gb300 import cases
+    case = cases.sedimentation(nx=16, ny=16, nz=32)
+    sim = oracle.OracleSim(case)
+    sim.neighbors()
+    pairs = _oracle_pairs(sim, case)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        sim.run(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return dict(value=pairs * 2 * steps / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{steps} full steps of sedimentation 16x16x32 ({len(case['x'])} particles, "
+                       f"{pairs} pairs/evaluation), FP64, single thread",
+                steps_per_s=steps / dt)
+
+
+def _oracle_pairs(sim, case):
+    ij = sim.pairs()
+    mob = case["type"] <= 1
+    return int(np.sum(mob[ij[:, 0]] | mob[ij[:, 1]]))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "native" else "gloo")
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ms = []
+        import oracle
+        from paper_2002_03120_gb300 import cases
+        case = cases.sedimentation(nx=16, ny=16, nz=32)
+        sim = oracle.OracleSim(case)
+        sim.neighbors()
+        pairs = _oracle_pairs(sim, case)
+        for _ in range(args.warmup):
+            sim.run(1)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            sim.run(1)
+            ms.append((time.perf_counter() - t0) * 1e3)
+        tot = sum(ms) / 1e3
+        val = pairs * 2 * args.steps / tot
+        sample = (f"sedimentation 16x16x32 ({len(case['x'])} particles) per step, the 32x32x64 "
+                  f"workload's physics at 1/8 of its lattice; FP64 oracle, single thread")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    main_r, other_r = time_native(args, ws, rank, local)
+    t_max = max_over_ranks(main_r["ms"], ws)
+    pairs = main_r["pairs"]
+    value = pairs * 2 * args.steps * ws / (t_max / 1e3)
+    steps_per_s = args.steps / (t_max / 1e3)
+    other_val = other_r["pairs"] * 2 * args.steps / (other_r["ms"] / 1e3)
+    peaks = measured_peaks()
+    # dominant kernel: the fluid force pass; FP64 ALU bound
+    force_flops = FLOPS_PER_PAIR * 2 * pairs  # ordered pairs ~ 2 x unordered
+    achieved_tf = force_flops / (main_r["force_ms"] / 1e3) / 1e12
+    sm_mhz = main_r["clocks"].get("sm_mhz") or 1440.0
+    # FP64 peak: 152 SMs x 2 DFMA/clk/SM (nominal 1.25 TFLOP/s at 2070 MHz), 2 flops per DFMA
+    fp64_peak_tf = 152 * 2 * 2 * 2070e6 / 1e12
+    rec = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 pairs / f64 state",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": main_r["N"], "pairs_per_eval": pairs,
+                   "evals_per_step": 2, "precision": args.precision,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{ws}"},
+        "timesteps_per_s": steps_per_s,
+        "gpu_launches": main_r["kernels"] * args.steps,
+        "clocks": main_r["clocks"],
+        "roofline": {"kernel": "k_force_fluid (force pass, velver 1)", "bound": "alu",
+                     "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp64_peak_tf, "traffic": None,
+                     "ms_per_launch": main_r["force_ms"],
+                     "note": "FP64 peak from unit counts x max clock (nominal)"},
+        "e2e": {"value": pairs * 2 / (main_r["e2e_ms"] / 1e3) * ws, "unit": UNIT,
+                "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
+        "split_precision" if args.precision == "fp64" else "fp64_path": {
+            "value": other_val, "unit": UNIT, "ms_per_step": other_r["ms"] / args.steps,
+            "force_ms_per_launch": other_r["force_ms"],
+            "speedup_vs_fp64": (other_val / (value / ws)) if args.precision == "fp64" else None},
+        "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(rec))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * sdpd.h -- C ABI of libsdpd, the GB300 (sm_103a) implementation of the
+ * per-timestep SDPD-DEM particle-interaction step of Tsuzuki, "DEMocritus: an
+ * open source framework for simulating slurry flows using an SDPD-DEM coupled
+ * model" (arXiv 2002.03120).
+ *
+ * One call of each stage below performs, on the GPU, the routine of the
+ * paper's Algorithm 1 (per velocity-Verlet sub-step "velver") or Algorithm 2
+ * (inside compute_force) named in its comment.  All stages are asynchronous on
+ * the CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy default
+ * stream) unless stated otherwise.
+ *
+ * Conventions
+ *  - Every function returns an sdpd_status; no C++ exception crosses the ABI
+ *    and no function calls exit, abort or a device trap.  On failure
+ *    sdpd_last_error() returns a message (thread-local).
+ *  - Errors raised by kernels (capacity overflow, non-finite state) are
+ *    recorded in a device word and reported by the next synchronising call
+ *    (sdpd_get_*, sdpd_check, sdpd_step) as SDPD_E_CAPACITY / SDPD_E_NONFINITE.
+ *  - Arrays are row-major [n][3] doubles (x, y, z) unless stated; pointers may
+ *    be host or device memory (unified addressing); the library copies what it
+ *    needs and never keeps or frees caller memory.
+ *  - A context owns all its device buffers (allocated by sdpd_init, released
+ *    by sdpd_destroy).  A context is not thread-safe; distinct contexts are
+ *    independent.
+ *  - Particle types: 0 fluid, 1 rigid (DEM sphere), 2 inner wall, 3 outer wall
+ *    (the frozen dummy particles of Section 2.5).
+ *  - Particle index within an instance = global id (gid) of the counter-based
+ *    noise (Philox4x32-10 keyed by the seed and the instance, counter
+ *    (min gid, max gid, step, block)).
+ */
+#ifndef SDPD_H
+#define SDPD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SDPD_OK = 0,
+    SDPD_E_INVALID = 1,   /* bad argument or parameter set                  */
+    SDPD_E_CUDA = 2,      /* a CUDA runtime call failed                      */
+    SDPD_E_OOM = 3,       /* device allocation failed                        */
+    SDPD_E_CAPACITY = 4,  /* neighbour list / cell / contact table overflow  */
+    SDPD_E_NONFINITE = 5, /* NaN or Inf detected in the state                */
+    SDPD_E_DOMAIN = 6,    /* particle left the grid on a wall axis           */
+    SDPD_E_TIMEOUT = 7,   /* a bounded device wait gave up                   */
+    SDPD_E_STATE = 8      /* stage called out of order                       */
+} sdpd_status;
+
+/* Pair-force precision of a context. */
+enum {
+    SDPD_PREC_FP64 = 0,   /* all pair arithmetic in double                     */
+    SDPD_PREC_SPLIT = 1   /* pair arithmetic in float; positions, momenta,
+                             density/pressure and the integrator in double    */
+};
+
+typedef struct sdpd_ctx sdpd_ctx;
+
+/* Parameters of one instance: Table 1 of the paper (Section 3.1) plus the
+ * constants of the readings where the paper is silent.  SI or mesoscale units,
+ * the caller's choice, as long as they are consistent. */
+typedef struct {
+    double dx;            /* initial particle spacing (--dx)                        */
+    double r_c;           /* kernel radius h: support of the Lucy kernel (--h)       */
+    double dt;            /* time step (--dt)                                        */
+    double rho0, p0, alpha, beta_p; /* Eq. prtcpres (--dens0 --pres0 --alpha --beta) */
+    double eta, xi, kBT;  /* shear and bulk viscosity, energy level (Section 2.1)   */
+    double coeff_c, coeff_d, coeff_r, coeff_t; /* --Coeff_fcij .. --Coeff_ftij       */
+    double origin[3], box[3]; /* domain (--orgx.. --Lx..); fluid region on wall axes */
+    double g[3];          /* uniform acceleration (--gx --gy --gz)                  */
+    double body_amp;      /* reverse-Poiseuille forcing (accel.): +amp on the lower,
+                             -amp on the upper half of split_axis (--gravity_type)  */
+    double artvis_alpha, artvis_e; /* collision-method range (x dx), restitution     */
+    double kn, restitution, nu_p, E_p, mu_fric; /* DEM (Section 2.2; --Edem --Pdem --Fdem) */
+    double lub_gap_min;   /* lubrication gap floor as a fraction of R_i + R_j       */
+    double eps_min;       /* lower clamp of the fluid volume fraction               */
+    int periodic[3];      /* per-axis periodic (1) or wall (0) (--periodic_type)    */
+    int body_axis, split_axis;
+    int pressure_filter, clamp_negative_p, artvis; /* switches (Sections 2.1, 2.5, 4.4) */
+    int dem_law;          /* 0: Eqs. deminputA-F as printed; 1: linear kn + restitution */
+    int pad_;
+    unsigned long long seed; /* noise seed                                          */
+} sdpd_params;
+
+/* Create a context for n_instances independent instances (batched viscometer
+ * sweep: one launch per stage covers all instances).  params[k] and
+ * n_particles[k] describe instance k.  precision: SDPD_PREC_*.  max_neighbors:
+ * capacity of each particle's neighbour list (0 = 384).  max_contacts: DEM
+ * contact-history slots per rigid particle (0 = 16).  Validates the parameters
+ * (gamma^a, gamma^b >= 0 i.e. 40 eta/51 <= xi <= 5 eta/3; periodic axes at
+ * least 3 kernel radii wide; positive dx, r_c, dt, rho0).  Allocates the
+ * device buffers.  Synchronous. */
+sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long long *n_particles,
+                      int precision, int max_neighbors, int max_contacts, sdpd_ctx **out);
+
+/* Release a context and all its device memory (NULL is ignored). */
+void sdpd_destroy(sdpd_ctx *ctx);
+
+/* Upload the particles of instance `inst` (n must equal its n_particles).
+ * x, v, w: [n][3]; type: [n] int32; radius, mass: [n].  Walls must have zero
+ * velocity and spin.  Resets the contact history of the instance.
+ * Synchronous. */
+sdpd_status sdpd_set_particles(sdpd_ctx *ctx, int inst, long long n, const double *x,
+                               const double *v, const double *w, const int *type,
+                               const double *radius, const double *mass);
+
+/* Upload positions, velocities and spins of all instances at once ([N][3],
+ * N = sum of n_particles; any pointer may be NULL to keep that field).
+ * Asynchronous on `stream` (host memory should be pinned). */
+sdpd_status sdpd_upload_state(sdpd_ctx *ctx, const double *x, const double *v, const double *w,
+                              void *stream);
+
+/* Download positions, velocities, spins, total force and torque of all
+ * instances ([N][3]; NULL skips a field).  Asynchronous on `stream`. */
+sdpd_status sdpd_download_state(sdpd_ctx *ctx, double *x, double *v, double *w, double *F,
+                                double *N, void *stream);
+
+/* Set the time-step counter (keys the random stream).  Synchronous. */
+sdpd_status sdpd_set_step(sdpd_ctx *ctx, long long step);
+sdpd_status sdpd_get_step(sdpd_ctx *ctx, long long *step);
+
+/* compute_neighbor_list (Algorithm 1; Section 3.2): background grid of cells
+ * at least max(h, largest sphere diameter) wide, counting sort of the
+ * particles into Morton-ranked cells (deterministic order within a cell), the
+ * cell-sorted particle mirrors, and each particle's list of neighbours
+ * j != i with r_ij < h (plus rigid pairs in contact beyond h).  Neighbour
+ * decisions are exact in double precision. */
+sdpd_status sdpd_build_cells(sdpd_ctx *ctx, void *stream);
+
+/* compute_particle_dens, compute_particle_pres, smoothe_particle_pres
+ * (Algorithm 1; Eqs. compdens, prtcpres; pressure filter): number density
+ * d_i = C_n sum_j W_ij (self included), rho_i = rho0 dx^3 d_i, pressure from
+ * the equation of state (clamped at 0 if clamp_negative_p), Shepard-filtered if
+ * pressure_filter; also the fluid sums each rigid particle needs for the drag.
+ * Requires sdpd_build_cells for the current positions. */
+sdpd_status sdpd_compute_density(sdpd_ctx *ctx, void *stream);
+
+/* compute_fpi_action (Algorithm 2; Eqs. fvfdef, beta, F_fpi_DG): per rigid
+ * particle the fluid volume fraction, the mean fluid velocity around it and
+ * the drag force.  Requires sdpd_compute_density. */
+sdpd_status sdpd_couple_drag(sdpd_ctx *ctx, void *stream);
+
+/* compute_fluid + compute_fpi_reaction + compute_rigid (Algorithm 2; Eqs.
+ * FijC, FijD, FijR, FijT, F_fpi_PG, F_fpi_DG_reac, dem_fnij .. slideref,
+ * lubri) and the external force (Eq. govern): total force and torque of every
+ * particle for velocity-Verlet sub-step `velver` (1 or 2) at the current step
+ * counter.  velver 2 commits the tangential contact history.  Requires
+ * sdpd_couple_drag. */
+sdpd_status sdpd_compute_forces(sdpd_ctx *ctx, int velver, void *stream);
+
+/* update(velver) (Algorithm 1; Eqs. newton1, newton2): velocity-Verlet half
+ * kick of v and w; velver 1 also drifts x and applies the periodic wrap / wall
+ * reflection; velver 2 applies the artificial viscosity (collision method) if
+ * enabled and advances the step counter. */
+sdpd_status sdpd_integrate(sdpd_ctx *ctx, int velver, void *stream);
+
+/* Algorithm 1 for n_steps full steps (both sub-steps, all stages), replayed
+ * from a CUDA graph captured on the first call.  Positions unchanged since the
+ * last neighbour build (velver 1 after velver 2) reuse that build and its
+ * density exactly.  Synchronises at the end and reports kernel errors. */
+sdpd_status sdpd_step(sdpd_ctx *ctx, long long n_steps, void *stream);
+
+/* Reverse-Poiseuille viscometer read-out (Section 4.1; Eqs. poiseuanasol,
+ * poiseuave) of instance `inst`: mean velocity along body_axis of the fluid
+ * particles in n_bins slabs of split_axis (profile_out[n_bins], host), and the
+ * apparent viscosity mu = rho0 a D^2 / (12 V) from the mean speed V of the two
+ * counter-flowing halves (D = half the box).  Synchronous. */
+sdpd_status sdpd_viscosity_probe(sdpd_ctx *ctx, int inst, int n_bins, double *profile_out,
+                                 double *mu_app_out);
+
+/* Host copies of one instance's state (NULL skips a field): x, v, w, F, N
+ * [n][3]; d (number density), p (pressure) [n].  Synchronous. */
+sdpd_status sdpd_get_state(sdpd_ctx *ctx, int inst, double *x, double *v, double *w, double *F,
+                           double *N, double *d, double *p);
+
+/* Per rigid particle of instance `inst`, in gid order of the rigid particles:
+ * fluid volume fraction eps[nr], drag force F_dg[nr][3].  Synchronous. */
+sdpd_status sdpd_get_drag(sdpd_ctx *ctx, int inst, double *eps, double *F_dg);
+
+/* Neighbour pairs (i < j, instance-local gids) with r_ij < h of instance
+ * `inst` from the last build: writes min(cap, count) pairs into ij[2*cap] and
+ * the count into *n_out.  Synchronous. */
+sdpd_status sdpd_get_pairs(sdpd_ctx *ctx, int inst, long long cap, int *ij, long long *n_out);
+
+/* Number of unordered pairs within h that the force pass evaluates (at least
+ * one mobile particle), all instances, from the last build.  Synchronous. */
+sdpd_status sdpd_count_pairs(sdpd_ctx *ctx, long long *n_pairs);
+
+/* Diagnostics of instance `inst` (Synchronous): out[0..2] total momentum,
+ * out[3] kinetic energy, out[4] kinetic temperature m<v^2>/3 of the mobile
+ * particles (mean removed), out[5] max |v|, out[6] min d, out[7] max d,
+ * out[8] number of non-finite values in x, v, w. */
+sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
+
+/* Number of kernel nodes in the captured one-step graph of sdpd_step (0 if
+ * sdpd_step has not run yet).  Synchronous. */
+sdpd_status sdpd_graph_kernels(sdpd_ctx *ctx, long long *n_kernels);
+
+/* Wait for all work of the context and report a pending kernel error. */
+sdpd_status sdpd_check(sdpd_ctx *ctx);
+
+/* Last error message of the calling thread (never NULL). */
+const char *sdpd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDPD_H */

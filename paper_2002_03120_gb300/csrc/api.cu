@@ -1,0 +1,813 @@
+// api.cu -- the C ABI of libsdpd (include/sdpd.h): context life cycle,
+// parameter validation, per-instance grids, the stage sequence of
+// Algorithm 1 and its CUDA-graph replay.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace sdpd;
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+sdpd_status fail(sdpd_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(SDPD_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+struct HostInst {
+    sdpd_params P;
+    long long n = 0, begin = 0;
+    bool set = false;
+    double xmin[3] = { 0, 0, 0 }, xmax[3] = { 0, 0, 0 };
+    double Rmax = 0.0;
+    std::vector<int> type;
+};
+
+}  // namespace
+
+struct sdpd_ctx {
+    int n_inst = 0, precision = 0, cap = 384, K = 16;
+    long long N = 0, Npad = 0;
+    std::vector<HostInst> hi;
+    std::vector<Inst> inst;
+    Bufs b{};
+    std::vector<void *> allocs;        // fixed-size buffers
+    std::vector<void *> geo_allocs;    // buffers sized by the grid / rigid count
+    Inst *d_inst = nullptr;
+    int any_filter = 0, any_artvis = 0;
+    bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
+    int sticky_err = 0;
+    long long host_step = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaGraph_t graph_def = nullptr;
+};
+
+namespace {
+
+template <class T> sdpd_status dalloc(sdpd_ctx *c, T **p, size_t count, bool geo = false)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(SDPD_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    (geo ? c->geo_allocs : c->allocs).push_back((void *)*p);
+    return SDPD_OK;
+}
+
+#define ALLOC(ptr, n, geo)                                                                      \
+    do {                                                                                        \
+        sdpd_status s_ = dalloc(c, &(ptr), (size_t)(n), geo);                                   \
+        if (s_ != SDPD_OK) return s_;                                                           \
+    } while (0)
+
+void free_geo(sdpd_ctx *c)
+{
+    for (void *p : c->geo_allocs) cudaFree(p);
+    c->geo_allocs.clear();
+}
+
+void drop_graph(sdpd_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_def) cudaGraphDestroy(c->graph_def);
+    c->graph = nullptr;
+    c->graph_def = nullptr;
+}
+
+double lucy_W(double r, double h)
+{
+    if (r >= h) return 0.0;
+    const double q = r / h, om = 1.0 - q;
+    return 105.0 / (16.0 * PI * h * h * h) * (1.0 + 3.0 * q) * om * om * om;
+}
+
+// Normalisation of the kernel coefficient: C_n = 1 / (dx^3 * sum of W over a
+// perfect cubic lattice, self included).
+double kernel_norm(double dx, double h)
+{
+    const int m = (int)std::ceil(h / dx) + 1;
+    double s = 0.0;
+    for (int k = -m; k <= m; ++k)
+        for (int j = -m; j <= m; ++j)
+            for (int i = -m; i <= m; ++i) s += lucy_W(std::sqrt((double)(i * i + j * j + k * k)) * dx, h);
+    return 1.0 / (dx * dx * dx * s);
+}
+
+sdpd_status validate(const sdpd_params &p, int k)
+{
+    char buf[256];
+    auto bad = [&](const char *what) {
+        std::snprintf(buf, sizeof buf, "instance %d: %s", k, what);
+        return fail(SDPD_E_INVALID, buf);
+    };
+    if (!(p.dx > 0) || !(p.r_c > 0) || !(p.dt > 0) || !(p.rho0 > 0)) return bad("dx, r_c, dt, rho0 must be > 0");
+    if (!(p.eta >= 0) || !(p.kBT >= 0)) return bad("eta and kBT must be >= 0");
+    const double Ca = 20.0 * p.eta / 3.0 - 4.0 * p.xi, Cb = 17.0 * p.xi - 40.0 * p.eta / 3.0;
+    const double tol = 1e-12 * (p.eta > 0 ? p.eta : 1.0);
+    if (Ca < -tol || Cb < -tol) return bad("need 40 eta/51 <= xi <= 5 eta/3 (gamma^a, gamma^b >= 0)");
+    for (int a = 0; a < 3; ++a) {
+        if (!(p.box[a] > 0)) return bad("box must be > 0");
+        if (p.periodic[a] && p.box[a] < 3.0 * p.r_c) return bad("periodic axis narrower than 3 r_c");
+    }
+    if (p.body_axis < 0 || p.body_axis > 2 || p.split_axis < 0 || p.split_axis > 2) return bad("axis out of range");
+    if (p.dem_law == 1 && !(p.restitution > 0 && p.restitution <= 1)) return bad("restitution must be in (0, 1]");
+    if (p.dem_law == 0 && !(p.E_p > 0)) return bad("E_p must be > 0 for dem_law 0");
+    if (p.mu_fric < 0) return bad("mu_fric must be >= 0");
+    return SDPD_OK;
+}
+
+uint32_t morton(int x, int y, int z)
+{
+    return morton_spread((uint32_t)x) | (morton_spread((uint32_t)y) << 1) | (morton_spread((uint32_t)z) << 2);
+}
+
+// Grids, Morton ranks, rigid lists and the per-instance constants; sized
+// buffers are (re)allocated here.
+sdpd_status prepare(sdpd_ctx *c)
+{
+    for (int k = 0; k < c->n_inst; ++k)
+        if (!c->hi[k].set) return fail(SDPD_E_STATE, "sdpd_set_particles not called for every instance");
+    drop_graph(c);
+    free_geo(c);
+    c->inst.assign(c->n_inst, Inst{});
+    std::vector<int> rank_all;
+    int cell_base = 0;
+    for (int k = 0; k < c->n_inst; ++k) {
+        const HostInst &H = c->hi[k];
+        const sdpd_params &p = H.P;
+        Inst &I = c->inst[k];
+        std::memset(&I, 0, sizeof(I));
+        const double cmin = std::max(p.r_c, 2.0 * H.Rmax);
+        for (int a = 0; a < 3; ++a) {
+            I.origin[a] = p.origin[a];
+            I.box[a] = p.box[a];
+            I.periodic[a] = p.periodic[a] ? 1 : 0;
+            if (p.periodic[a]) {
+                int nc = (int)std::floor(p.box[a] / cmin);
+                if (nc < 3) {
+                    char buf[160];
+                    std::snprintf(buf, sizeof buf,
+                                  "instance %d axis %d: periodic box must hold 3 cells of max(h, 2 R_max)", k, a);
+                    return fail(SDPD_E_INVALID, buf);
+                }
+                I.nc[a] = nc;
+                I.cs[a] = p.box[a] / nc;
+                I.lo[a] = p.origin[a];
+            } else {
+                const double lo = std::min(H.xmin[a], p.origin[a]) - 0.5 * cmin;
+                const double hi = std::max(H.xmax[a], p.origin[a] + p.box[a]) + 0.5 * cmin;
+                I.cs[a] = cmin;
+                I.lo[a] = lo;
+                I.nc[a] = (int)std::ceil((hi - lo) / cmin);
+            }
+            if (I.nc[a] > 1023) return fail(SDPD_E_INVALID, "more than 1023 cells on an axis");
+            I.inv_cs[a] = 1.0 / I.cs[a];
+            I.csf[a] = (float)I.cs[a];
+        }
+        I.ncell = I.nc[0] * I.nc[1] * I.nc[2];
+        I.cell_base = cell_base;
+        // Morton rank of each linear cell
+        std::vector<std::pair<uint32_t, int>> codes(I.ncell);
+        for (int z = 0; z < I.nc[2]; ++z)
+            for (int y = 0; y < I.nc[1]; ++y)
+                for (int x = 0; x < I.nc[0]; ++x) {
+                    const int lin = (z * I.nc[1] + y) * I.nc[0] + x;
+                    codes[lin] = { morton(x, y, z), lin };
+                }
+        std::sort(codes.begin(), codes.end());
+        std::vector<int> rank(I.ncell);
+        for (int r = 0; r < I.ncell; ++r) rank[codes[r].second] = r;
+        rank_all.insert(rank_all.end(), rank.begin(), rank.end());
+        cell_base += I.ncell;
+        I.p_begin = H.begin;
+        I.p_end = H.begin + H.n;
+        // physics constants
+        const double h = p.r_c;
+        I.dx = p.dx; I.rc = h; I.rc2 = h * h; I.dt = p.dt; I.hdt = 0.5 * p.dt;
+        I.isqrt_dt = 1.0 / std::sqrt(p.dt);
+        I.Wc = 105.0 / (16.0 * PI * h * h * h);
+        I.Fc = 315.0 / (4.0 * PI * h * h * h * h * h);
+        I.W0 = I.Wc;
+        I.Cn = kernel_norm(p.dx, h);
+        I.mf = p.rho0 * p.dx * p.dx * p.dx;
+        I.inv_dx3 = 1.0 / (p.dx * p.dx * p.dx);
+        I.rho0 = p.rho0; I.p0 = p.p0; I.alpha = p.alpha; I.beta_p = p.beta_p;
+        I.eta = p.eta; I.kBT = p.kBT;
+        I.Ca = std::max(0.0, 20.0 * p.eta / 3.0 - 4.0 * p.xi);
+        I.Cb = std::max(0.0, 17.0 * p.xi - 40.0 * p.eta / 3.0);
+        I.Ka = 2.0 * std::sqrt(p.kBT * I.Ca * I.Fc);
+        I.Kb = 2.0 * std::sqrt(p.kBT * I.Cb * I.Fc);
+        I.coeff_c = p.coeff_c; I.coeff_d = p.coeff_d; I.coeff_r = p.coeff_r; I.coeff_t = p.coeff_t;
+        for (int a = 0; a < 3; ++a) I.g[a] = p.g[a];
+        I.body_amp = p.body_amp; I.body_axis = p.body_axis; I.split_axis = p.split_axis;
+        I.filter = p.pressure_filter ? 1 : 0; I.clamp = p.clamp_negative_p ? 1 : 0;
+        I.artvis = p.artvis ? 1 : 0; I.dem_law = p.dem_law;
+        I.noise = (p.coeff_t != 0.0 && p.kBT > 0.0) ? 1 : 0;
+        I.artvis_rlim = p.artvis_alpha * p.dx; I.artvis_e = p.artvis_e;
+        I.kn = p.kn; I.kt_ratio = 1.0 / (2.0 * (1.0 + p.nu_p));
+        if (p.dem_law == 1) {
+            const double le = std::log(p.restitution);
+            I.zeta = -le / std::sqrt(PI * PI + le * le);
+        }
+        I.nu_p = p.nu_p; I.E_p = p.E_p; I.mu_fric = p.mu_fric;
+        I.lub_gap_min = p.lub_gap_min; I.eps_min = p.eps_min;
+        I.Vf = 4.0 / 3.0 * PI * h * h * h;
+        I.lever_fluid = 0.5 * p.dx;
+        I.key0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
+        I.key1 = (uint32_t)(p.seed >> 32) ^ (uint32_t)k;
+        I.rcf = (float)h; I.inv_rcf = (float)(1.0 / h);
+        I.Wcf = (float)I.Wc; I.Fcf = (float)I.Fc; I.W0f = (float)I.W0;
+        I.Caf = (float)I.Ca; I.Cbf = (float)I.Cb; I.Kaf = (float)I.Ka; I.Kbf = (float)I.Kb;
+        I.isqrt_dtf = (float)I.isqrt_dt;
+        I.coeff_cf = (float)p.coeff_c; I.coeff_df = (float)p.coeff_d;
+        I.coeff_rf = (float)p.coeff_r; I.coeff_tf = (float)p.coeff_t;
+        I.lever_fluidf = (float)I.lever_fluid;
+        I.guard_lo = (float)(I.rc2 * (1.0 - 1e-5));
+        I.guard_hi = (float)(I.rc2 * (1.0 + 1e-5));
+    }
+    Bufs &b = c->b;
+    b.ncell_total = cell_base;
+    int *rank_d = nullptr;
+    ALLOC(rank_d, cell_base, true);
+    CUDA_TRY(cudaMemcpy(rank_d, rank_all.data(), sizeof(int) * cell_base, cudaMemcpyHostToDevice));
+    b.cell_rank = rank_d;
+    ALLOC(b.ccount, cell_base, true);
+    ALLOC(b.cstart, cell_base + 1, true);
+    ALLOC(b.scan_partials, (cell_base + 1023) / 1024 + 1, true);
+    // rigid lists (gid order)
+    std::vector<int> rigid_gid, rigid_of(c->N, -1);
+    for (int k = 0; k < c->n_inst; ++k) {
+        const HostInst &H = c->hi[k];
+        for (long long i = 0; i < H.n; ++i)
+            if (H.type[i] == T_RIGID) {
+                rigid_of[H.begin + i] = (int)rigid_gid.size();
+                rigid_gid.push_back((int)(H.begin + i));
+            }
+    }
+    b.nrigid = (int)rigid_gid.size();
+    ALLOC(b.rigid_gid, b.nrigid, true);
+    ALLOC(b.rigid_of, c->N, true);
+    if (b.nrigid) CUDA_TRY(cudaMemcpy(b.rigid_gid, rigid_gid.data(), sizeof(int) * b.nrigid, cudaMemcpyHostToDevice));
+    if (c->N) CUDA_TRY(cudaMemcpy(b.rigid_of, rigid_of.data(), sizeof(int) * c->N, cudaMemcpyHostToDevice));
+    ALLOC(b.eps, b.nrigid, true);
+    ALLOC(b.fdg, 3 * (size_t)b.nrigid, true);
+    const size_t nk = (size_t)b.nrigid * c->K;
+    ALLOC(b.h_n, b.nrigid, true);
+    ALLOC(b.hn_n, b.nrigid, true);
+    ALLOC(b.h_part, nk, true);
+    ALLOC(b.hn_part, nk, true);
+    ALLOC(b.h_del, 3 * nk, true);
+    ALLOC(b.hn_del, 3 * nk, true);
+    CUDA_TRY(cudaMemset(b.h_n, 0, sizeof(int) * (b.nrigid ? b.nrigid : 1)));
+    CUDA_TRY(cudaMemset(b.hn_n, 0, sizeof(int) * (b.nrigid ? b.nrigid : 1)));
+    CUDA_TRY(cudaMemset(b.eps, 0, sizeof(double) * (b.nrigid ? b.nrigid : 1)));
+    CUDA_TRY(cudaMemset(b.fdg, 0, sizeof(double) * 3 * (b.nrigid ? b.nrigid : 1)));
+    if (!c->d_inst) {
+        sdpd_status s = dalloc(c, &c->d_inst, c->n_inst, false);
+        if (s != SDPD_OK) return s;
+    }
+    CUDA_TRY(cudaMemcpy(c->d_inst, c->inst.data(), sizeof(Inst) * c->n_inst, cudaMemcpyHostToDevice));
+    b.inst = c->d_inst;
+    c->any_filter = 0;
+    c->any_artvis = 0;
+    for (auto &I : c->inst) {
+        c->any_filter |= I.filter;
+        c->any_artvis |= I.artvis;
+    }
+    c->geometry_ready = true;
+    c->cells_valid = c->density_valid = c->drag_valid = false;
+    return SDPD_OK;
+}
+
+sdpd_status check_err(sdpd_ctx *c)
+{
+    int e = 0;
+    CUDA_TRY(cudaMemcpy(&e, c->b.err, sizeof(int), cudaMemcpyDeviceToHost));
+    c->sticky_err |= e;
+    e = c->sticky_err;
+    if (!e) return SDPD_OK;
+    if (e & ERR_NBR_CAP) return fail(SDPD_E_CAPACITY, "neighbour list capacity exceeded (raise max_neighbors)");
+    if (e & ERR_CONTACT_CAP) return fail(SDPD_E_CAPACITY, "contact history capacity exceeded (raise max_contacts)");
+    if (e & ERR_CELL_CAP) return fail(SDPD_E_CAPACITY, "cell capacity exceeded");
+    if (e & ERR_NONFINITE) return fail(SDPD_E_NONFINITE, "non-finite position, velocity or spin");
+    if (e & ERR_DOMAIN) return fail(SDPD_E_DOMAIN, "particle outside the grid on a wall axis");
+    return fail(SDPD_E_CUDA, "unknown device error");
+}
+
+sdpd_status ensure_geometry(sdpd_ctx *c)
+{
+    if (!c->geometry_ready) return prepare(c);
+    return SDPD_OK;
+}
+
+void enqueue_build(sdpd_ctx *c, cudaStream_t st)
+{
+    launch_cell_keys(c->b, st);
+    launch_scan_cells(c->b, st);
+    launch_scatter_rank(c->b, st);
+    launch_gather(c->b, c->precision, st);
+    launch_neighbors(c->b, c->precision, st);
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+const char *sdpd_last_error(void) { return g_last_error.c_str(); }
+
+sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long long *n_particles,
+                      int precision, int max_neighbors, int max_contacts, sdpd_ctx **out)
+{
+    if (!out) return fail(SDPD_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!params || !n_particles || n_instances < 1) return fail(SDPD_E_INVALID, "bad instance list");
+    if (precision != SDPD_PREC_FP64 && precision != SDPD_PREC_SPLIT) return fail(SDPD_E_INVALID, "bad precision");
+    for (int k = 0; k < n_instances; ++k) {
+        if (n_particles[k] < 0) return fail(SDPD_E_INVALID, "negative particle count");
+        sdpd_status s = validate(params[k], k);
+        if (s != SDPD_OK) return s;
+    }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+        return fail(SDPD_E_CUDA, "no CUDA device");
+    sdpd_ctx *c = new sdpd_ctx();
+    c->n_inst = n_instances;
+    c->precision = precision;
+    c->cap = max_neighbors > 0 ? max_neighbors : 384;
+    c->K = max_contacts > 0 ? max_contacts : 16;
+    c->hi.resize(n_instances);
+    long long N = 0;
+    for (int k = 0; k < n_instances; ++k) {
+        c->hi[k].P = params[k];
+        c->hi[k].n = n_particles[k];
+        c->hi[k].begin = N;
+        N += n_particles[k];
+    }
+    if (N >= (1LL << 31) - 1) {
+        delete c;
+        return fail(SDPD_E_INVALID, "more than 2^31 particles");
+    }
+    c->N = N;
+    c->Npad = (N + 127) / 128 * 128;
+    Bufs &b = c->b;
+    b.N = N;
+    b.Npad = c->Npad;
+    b.n_inst = n_instances;
+    b.cap = c->cap;
+    b.K = c->K;
+    auto cleanup = [&](sdpd_status s) {
+        sdpd_destroy(c);
+        return s;
+    };
+#define IALLOC(ptr, n)                                                                          \
+    do {                                                                                        \
+        sdpd_status s_ = dalloc(c, &(ptr), (size_t)(n), false);                                 \
+        if (s_ != SDPD_OK) return cleanup(s_);                                                  \
+    } while (0)
+    const size_t n3 = 3 * (size_t)N;
+    IALLOC(b.x, n3); IALLOC(b.v, n3); IALLOC(b.w, n3); IALLOC(b.F, n3); IALLOC(b.T, n3);
+    IALLOC(b.dv, n3);
+    IALLOC(b.type, N); IALLOC(b.pinst, N);
+    IALLOC(b.R, N); IALLOC(b.m, N); IALLOC(b.Iner, N);
+    IALLOC(b.key, N); IALLOC(b.slot_in_cell, N); IALLOC(b.tmp_perm, N); IALLOC(b.perm, N);
+    IALLOC(b.slot_of, N); IALLOC(b.stype, N);
+    IALLOC(b.sd, N); IALLOC(b.sp, N); IALLOC(b.sp2, N);
+    IALLOC(b.rxn, N);
+    if (precision == SDPD_PREC_SPLIT) {
+        IALLOC(b.A32, N); IALLOC(b.B32, N); IALLOC(b.C32, N); IALLOC(b.D32, N);
+    } else {
+        IALLOC(b.A64, N); IALLOC(b.B64, N); IALLOC(b.C64, N); IALLOC(b.D64, N);
+    }
+    IALLOC(b.nbr, (size_t)c->cap * c->Npad);
+    IALLOC(b.ncnt, N);
+    IALLOC(b.step, 1); IALLOC(b.err, 1); IALLOC(b.pair_count, 1);
+    IALLOC(b.probe, 4096 * 2 + 64);
+#undef IALLOC
+    if (cudaMemset(b.err, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.step, 0, sizeof(long long)) != cudaSuccess ||
+        cudaMemset(b.F, 0, sizeof(double) * (n3 ? n3 : 1)) != cudaSuccess ||
+        cudaMemset(b.T, 0, sizeof(double) * (n3 ? n3 : 1)) != cudaSuccess)
+        return cleanup(fail(SDPD_E_CUDA, "cudaMemset failed"));
+    // per-instance pinst
+    std::vector<int> pinst(N);
+    for (int k = 0; k < n_instances; ++k)
+        for (long long i = 0; i < n_particles[k]; ++i) pinst[c->hi[k].begin + i] = k;
+    if (N && cudaMemcpy(b.pinst, pinst.data(), sizeof(int) * N, cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(fail(SDPD_E_CUDA, "cudaMemcpy pinst"));
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(fail(SDPD_E_CUDA, "cudaStreamCreate"));
+    *out = c;
+    return SDPD_OK;
+}
+
+void sdpd_destroy(sdpd_ctx *c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    drop_graph(c);
+    free_geo(c);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+sdpd_status sdpd_set_particles(sdpd_ctx *c, int inst, long long n, const double *x, const double *v,
+                               const double *w, const int *type, const double *radius, const double *mass)
+{
+    if (!c || inst < 0 || inst >= c->n_inst) return fail(SDPD_E_INVALID, "bad context or instance");
+    HostInst &H = c->hi[inst];
+    if (n != H.n) return fail(SDPD_E_INVALID, "particle count differs from sdpd_init");
+    if (n && (!x || !v || !w || !type || !radius || !mass)) return fail(SDPD_E_INVALID, "NULL array");
+    const size_t n3 = 3 * (size_t)n;
+    std::vector<double> hx(n3), hv(n3), hw(n3), hR(n), hm(n), hI(n);
+    std::vector<int> ht(n);
+    if (n) {
+        CUDA_TRY(cudaMemcpy(hx.data(), x, sizeof(double) * n3, cudaMemcpyDefault));
+        CUDA_TRY(cudaMemcpy(hv.data(), v, sizeof(double) * n3, cudaMemcpyDefault));
+        CUDA_TRY(cudaMemcpy(hw.data(), w, sizeof(double) * n3, cudaMemcpyDefault));
+        CUDA_TRY(cudaMemcpy(ht.data(), type, sizeof(int) * n, cudaMemcpyDefault));
+        CUDA_TRY(cudaMemcpy(hR.data(), radius, sizeof(double) * n, cudaMemcpyDefault));
+        CUDA_TRY(cudaMemcpy(hm.data(), mass, sizeof(double) * n, cudaMemcpyDefault));
+    }
+    const sdpd_params &p = H.P;
+    double Rmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        H.xmin[a] = 1e300;
+        H.xmax[a] = -1e300;
+    }
+    for (long long i = 0; i < n; ++i) {
+        const int t = ht[i];
+        if (t < 0 || t > 3) return fail(SDPD_E_INVALID, "particle type must be 0..3");
+        if (!(hm[i] > 0.0)) return fail(SDPD_E_INVALID, "particle mass must be > 0");
+        for (int a = 0; a < 3; ++a) {
+            const double xa = hx[3 * i + a];
+            if (!std::isfinite(xa)) return fail(SDPD_E_NONFINITE, "non-finite input position");
+            if (p.periodic[a] && (xa < p.origin[a] || xa >= p.origin[a] + p.box[a]))
+                return fail(SDPD_E_DOMAIN, "position outside the periodic box");
+            H.xmin[a] = std::min(H.xmin[a], xa);
+            H.xmax[a] = std::max(H.xmax[a], xa);
+        }
+        if (t == T_RIGID) {
+            if (!(hR[i] > 0.0)) return fail(SDPD_E_INVALID, "rigid radius must be > 0");
+            Rmax = std::max(Rmax, hR[i]);
+        }
+        // moment of inertia of a solid sphere, 2/5 m a^2, a = R (rigid) or
+        // dx/2 (fluid): the --iner input of Table 1 has no printed value
+        const double arm = (t == T_RIGID) ? hR[i] : 0.5 * p.dx;
+        hI[i] = 0.4 * hm[i] * arm * arm;
+    }
+    if (Rmax != H.Rmax || !H.set) c->geometry_ready = false;
+    H.Rmax = Rmax;
+    H.type = ht;
+    H.set = true;
+    Bufs &b = c->b;
+    const long long o = H.begin;
+    if (n) {
+        CUDA_TRY(cudaMemcpy(b.x + 3 * o, hx.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.v + 3 * o, hv.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.w + 3 * o, hw.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.type + o, ht.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.R + o, hR.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.m + o, hm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.Iner + o, hI.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemset(b.F + 3 * o, 0, sizeof(double) * n3));
+        CUDA_TRY(cudaMemset(b.T + 3 * o, 0, sizeof(double) * n3));
+    }
+    // the grid depends on the extents on wall axes: always re-derive it
+    c->geometry_ready = false;
+    c->cells_valid = c->density_valid = c->drag_valid = false;
+    c->sticky_err = 0;
+    CUDA_TRY(cudaMemset(b.err, 0, sizeof(int)));
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_upload_state(sdpd_ctx *c, const double *x, const double *v, const double *w, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
+    if (x) CUDA_TRY(cudaMemcpyAsync(c->b.x, x, bytes, cudaMemcpyDefault, st));
+    if (v) CUDA_TRY(cudaMemcpyAsync(c->b.v, v, bytes, cudaMemcpyDefault, st));
+    if (w) CUDA_TRY(cudaMemcpyAsync(c->b.w, w, bytes, cudaMemcpyDefault, st));
+    c->cells_valid = c->density_valid = c->drag_valid = false;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_download_state(sdpd_ctx *c, double *x, double *v, double *w, double *F, double *N, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
+    if (x) CUDA_TRY(cudaMemcpyAsync(x, c->b.x, bytes, cudaMemcpyDefault, st));
+    if (v) CUDA_TRY(cudaMemcpyAsync(v, c->b.v, bytes, cudaMemcpyDefault, st));
+    if (w) CUDA_TRY(cudaMemcpyAsync(w, c->b.w, bytes, cudaMemcpyDefault, st));
+    if (F) CUDA_TRY(cudaMemcpyAsync(F, c->b.F, bytes, cudaMemcpyDefault, st));
+    if (N) CUDA_TRY(cudaMemcpyAsync(N, c->b.T, bytes, cudaMemcpyDefault, st));
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_set_step(sdpd_ctx *c, long long step)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(c->b.step, &step, sizeof(long long), cudaMemcpyHostToDevice));
+    c->host_step = step;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_get_step(sdpd_ctx *c, long long *step)
+{
+    if (!c || !step) return fail(SDPD_E_INVALID, "NULL argument");
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(step, c->b.step, sizeof(long long), cudaMemcpyDeviceToHost));
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_build_cells(sdpd_ctx *c, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    sdpd_status s = ensure_geometry(c);
+    if (s != SDPD_OK) return s;
+    enqueue_build(c, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    c->cells_valid = true;
+    c->density_valid = c->drag_valid = false;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (!c->cells_valid) return fail(SDPD_E_STATE, "sdpd_build_cells must precede sdpd_compute_density");
+    launch_density(c->b, c->precision, c->any_filter, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    c->density_valid = true;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_couple_drag(sdpd_ctx *c, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (!c->density_valid) return fail(SDPD_E_STATE, "sdpd_compute_density must precede sdpd_couple_drag");
+    launch_drag(c->b, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    c->drag_valid = true;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_compute_forces(sdpd_ctx *c, int velver, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (velver != 1 && velver != 2) return fail(SDPD_E_INVALID, "velver must be 1 or 2");
+    if (!c->drag_valid) return fail(SDPD_E_STATE, "sdpd_couple_drag must precede sdpd_compute_forces");
+    launch_forces(c->b, c->precision, velver, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_integrate(sdpd_ctx *c, int velver, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (velver != 1 && velver != 2) return fail(SDPD_E_INVALID, "velver must be 1 or 2");
+    if (!c->geometry_ready || !c->b.inst) return fail(SDPD_E_STATE, "no forces computed yet");
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_integrate(c->b, c->precision, velver, c->any_artvis, st);
+    if (velver == 2) {
+        launch_step_done(c->b, st);
+        c->host_step += 1;
+    }
+    CUDA_TRY(cudaGetLastError());
+    if (velver == 1) c->cells_valid = c->density_valid = false;
+    c->drag_valid = false;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (n_steps < 0) return fail(SDPD_E_INVALID, "negative step count");
+    cudaStream_t st = (cudaStream_t)stream;
+    sdpd_status s = ensure_geometry(c);
+    if (s != SDPD_OK) return s;
+    if (!c->cells_valid) {
+        enqueue_build(c, st);
+        c->cells_valid = true;
+        c->density_valid = false;
+    }
+    if (!c->density_valid) {
+        launch_density(c->b, c->precision, c->any_filter, st);
+        c->density_valid = true;
+    }
+    if (!c->graph) {
+        // one full step; positions are unchanged between the velver-2 build
+        // and the next step's velver 1, so that sub-step reuses the build and
+        // the density exactly
+        CUDA_TRY(cudaStreamSynchronize(st));
+        CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaStream_t cs = c->cap_stream;
+        launch_drag(c->b, cs);
+        launch_forces(c->b, c->precision, 1, cs);
+        launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
+        enqueue_build(c, cs);
+        launch_density(c->b, c->precision, c->any_filter, cs);
+        launch_drag(c->b, cs);
+        launch_forces(c->b, c->precision, 2, cs);
+        launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);
+        launch_step_done(c->b, cs);
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &c->graph_def);
+        if (e != cudaSuccess) return fail(SDPD_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph, c->graph_def, 0);
+        if (e != cudaSuccess) return fail(SDPD_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    for (long long k = 0; k < n_steps; ++k) CUDA_TRY(cudaGraphLaunch(c->graph, st));
+    c->host_step += n_steps;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->cells_valid = c->density_valid = true;
+    c->drag_valid = false;
+    return check_err(c);
+}
+
+sdpd_status sdpd_graph_kernels(sdpd_ctx *c, long long *n_kernels)
+{
+    if (!c || !n_kernels) return fail(SDPD_E_INVALID, "bad argument");
+    *n_kernels = 0;
+    if (!c->graph_def) return SDPD_OK;
+    size_t n = 0;
+    CUDA_TRY(cudaGraphGetNodes(c->graph_def, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CUDA_TRY(cudaGraphGetNodes(c->graph_def, nodes.data(), &n));
+    long long k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+        k += (t == cudaGraphNodeTypeKernel);
+    }
+    *n_kernels = k;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_check(sdpd_ctx *c)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    CUDA_TRY(cudaDeviceSynchronize());
+    return check_err(c);
+}
+
+sdpd_status sdpd_viscosity_probe(sdpd_ctx *c, int inst, int n_bins, double *profile_out, double *mu_app_out)
+{
+    if (!c || inst < 0 || inst >= c->n_inst) return fail(SDPD_E_INVALID, "bad context or instance");
+    if (n_bins < 1 || n_bins > 4096) return fail(SDPD_E_INVALID, "n_bins must be in 1..4096");
+    sdpd_status s = ensure_geometry(c);
+    if (s != SDPD_OK) return s;
+    CUDA_TRY(cudaDeviceSynchronize());
+    launch_probe(c->b, inst, n_bins, 0, c->hi[inst].n);
+    std::vector<double> h(2 * n_bins + 4);
+    CUDA_TRY(cudaMemcpy(h.data(), c->b.probe, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < n_bins; ++k)
+        if (profile_out) profile_out[k] = h[n_bins + k] > 0 ? h[k] / h[n_bins + k] : 0.0;
+    const sdpd_params &p = c->hi[inst].P;
+    const double V = 0.5 * (h[2 * n_bins] / std::max(h[2 * n_bins + 2], 1.0) +
+                            h[2 * n_bins + 1] / std::max(h[2 * n_bins + 3], 1.0));
+    const double D = 0.5 * p.box[p.split_axis];
+    if (mu_app_out) *mu_app_out = p.rho0 * p.body_amp * D * D / (12.0 * V);
+    return check_err(c);
+}
+
+sdpd_status sdpd_get_state(sdpd_ctx *c, int inst, double *x, double *v, double *w, double *F, double *N,
+                           double *d, double *p)
+{
+    if (!c || inst < 0 || inst >= c->n_inst) return fail(SDPD_E_INVALID, "bad context or instance");
+    CUDA_TRY(cudaDeviceSynchronize());
+    const HostInst &H = c->hi[inst];
+    const size_t n3 = 3 * (size_t)H.n;
+    const long long o = H.begin;
+    if (H.n) {
+        if (x) CUDA_TRY(cudaMemcpy(x, c->b.x + 3 * o, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+        if (v) CUDA_TRY(cudaMemcpy(v, c->b.v + 3 * o, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+        if (w) CUDA_TRY(cudaMemcpy(w, c->b.w + 3 * o, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+        if (F) CUDA_TRY(cudaMemcpy(F, c->b.F + 3 * o, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+        if (N) CUDA_TRY(cudaMemcpy(N, c->b.T + 3 * o, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+        if ((d || p) && c->density_valid) {
+            std::vector<int> slot(H.n);
+            std::vector<double> sd(c->N), sp(c->N);
+            CUDA_TRY(cudaMemcpy(slot.data(), c->b.slot_of + o, sizeof(int) * H.n, cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemcpy(sd.data(), c->b.sd, sizeof(double) * c->N, cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemcpy(sp.data(), c->b.sp2, sizeof(double) * c->N, cudaMemcpyDeviceToHost));
+            for (long long i = 0; i < H.n; ++i) {
+                if (d) d[i] = sd[slot[i]];
+                if (p) p[i] = sp[slot[i]];
+            }
+        } else if (d || p) {
+            return fail(SDPD_E_STATE, "density not computed for the current positions");
+        }
+    }
+    return check_err(c);
+}
+
+sdpd_status sdpd_get_drag(sdpd_ctx *c, int inst, double *eps, double *F_dg)
+{
+    if (!c || inst < 0 || inst >= c->n_inst) return fail(SDPD_E_INVALID, "bad context or instance");
+    CUDA_TRY(cudaDeviceSynchronize());
+    const HostInst &H = c->hi[inst];
+    int r0 = 0, nr = 0;
+    for (int k = 0; k < c->n_inst; ++k) {
+        int cnt = 0;
+        for (int t : c->hi[k].type) cnt += (t == T_RIGID);
+        if (k < inst) r0 += cnt;
+        if (k == inst) nr = cnt;
+    }
+    (void)H;
+    if (nr) {
+        if (eps) CUDA_TRY(cudaMemcpy(eps, c->b.eps + r0, sizeof(double) * nr, cudaMemcpyDeviceToHost));
+        if (F_dg) CUDA_TRY(cudaMemcpy(F_dg, c->b.fdg + 3 * r0, sizeof(double) * 3 * nr, cudaMemcpyDeviceToHost));
+    }
+    return check_err(c);
+}
+
+sdpd_status sdpd_get_pairs(sdpd_ctx *c, int inst, long long cap, int *ij, long long *n_out)
+{
+    if (!c || inst < 0 || inst >= c->n_inst || !n_out) return fail(SDPD_E_INVALID, "bad argument");
+    if (!c->cells_valid) return fail(SDPD_E_STATE, "no neighbour build for the current positions");
+    CUDA_TRY(cudaDeviceSynchronize());
+    const long long N = c->N;
+    std::vector<int> cnt(N), perm(N), pinst(N);
+    CUDA_TRY(cudaMemcpy(cnt.data(), c->b.ncnt, sizeof(int) * N, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(perm.data(), c->b.perm, sizeof(int) * N, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(pinst.data(), c->b.pinst, sizeof(int) * N, cudaMemcpyDeviceToHost));
+    int kmax = 0;
+    for (long long s = 0; s < N; ++s) kmax = std::max(kmax, cnt[s]);
+    std::vector<int> nb((size_t)kmax * c->Npad);
+    if (kmax) CUDA_TRY(cudaMemcpy(nb.data(), c->b.nbr, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost));
+    const long long o = c->hi[inst].begin;
+    long long k = 0;
+    for (long long s = 0; s < N; ++s) {
+        const int gi = perm[s];
+        if (pinst[gi] != inst) continue;
+        for (int q = 0; q < cnt[s]; ++q) {
+            const uint32_t e = (uint32_t)nb[(size_t)q * c->Npad + s];
+            if (e & NB_FAR) continue;
+            const int gj = perm[e];
+            if (gj <= gi) continue;
+            if (k < cap && ij) {
+                ij[2 * k] = (int)(gi - o);
+                ij[2 * k + 1] = (int)(gj - o);
+            }
+            ++k;
+        }
+    }
+    *n_out = k;
+    return check_err(c);
+}
+
+sdpd_status sdpd_count_pairs(sdpd_ctx *c, long long *n_pairs)
+{
+    if (!c || !n_pairs) return fail(SDPD_E_INVALID, "bad argument");
+    if (!c->cells_valid) return fail(SDPD_E_STATE, "no neighbour build for the current positions");
+    launch_count_pairs(c->b, 0);
+    unsigned long long h = 0;
+    CUDA_TRY(cudaMemcpy(&h, c->b.pair_count, sizeof(h), cudaMemcpyDeviceToHost));
+    *n_pairs = (long long)h;
+    return check_err(c);
+}
+
+sdpd_status sdpd_diagnostics(sdpd_ctx *c, int inst, double out[16])
+{
+    if (!c || inst < 0 || inst >= c->n_inst || !out) return fail(SDPD_E_INVALID, "bad argument");
+    sdpd_status s = ensure_geometry(c);
+    if (s != SDPD_OK) return s;
+    CUDA_TRY(cudaDeviceSynchronize());
+    launch_diag(c->b, inst, 0, c->hi[inst].n);
+    double h[16];
+    CUDA_TRY(cudaMemcpy(h, c->b.probe, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 16; ++k) out[k] = 0.0;
+    out[0] = h[0]; out[1] = h[1]; out[2] = h[2];
+    out[3] = 0.5 * h[3];
+    const double M = h[4], n = h[5];
+    const double P2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    out[4] = n > 0 ? (h[3] - (M > 0 ? P2 / M : 0.0)) / (3.0 * n) : 0.0;
+    out[5] = h[6];
+    out[6] = h[7];
+    out[7] = h[8];
+    out[8] = h[9];
+    return check_err(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// common.cuh -- device data layout and helpers of libsdpd (sm_103a).
+//
+// Layout in HBM (one context, all instances concatenated):
+//   master state, gid order  : x, v, w, F, T (double [N][3]); type, inst (int);
+//                              mass props (double); rigid index maps
+//   cell tables              : per-instance grids, Morton-ranked cell keys,
+//                              cell counts / starts (counting sort)
+//   sorted mirrors, slot order (rebuilt by each neighbour build):
+//     split precision : A32 {x,y,z relative to own cell, bits(type|cell)}
+//                       B32 {v, R}   C32 {w, m}   D32 {p/d^2, 1/d, 1/sqrt d, gid}
+//     fp64            : A64 {x,y,z absolute, -} B64 C64 D64 likewise in double
+//   neighbour list, column-major nbr[k * Npad + slot] (coalesced per warp)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sdpd.h"
+
+namespace sdpd {
+
+constexpr int T_FLUID = 0, T_RIGID = 1, T_INNER = 2, T_OUTER = 3;
+constexpr double PI = 3.14159265358979323846;
+
+// device error word bits
+constexpr int ERR_NBR_CAP = 1, ERR_CELL_CAP = 2, ERR_CONTACT_CAP = 4, ERR_NONFINITE = 8,
+              ERR_DOMAIN = 16;
+
+// rigid-pair list entries beyond h (contact only) carry this flag
+constexpr uint32_t NB_FAR = 0x80000000u;
+constexpr int PLANE_BASE = -16;   // contact-history partner codes of wall planes
+
+// Per-instance constants, derived on the host from sdpd_params.
+struct Inst {
+    double origin[3], box[3], lo[3], cs[3], inv_cs[3];
+    int nc[3], periodic[3];
+    int cell_base, ncell;
+    long long p_begin, p_end;
+    double dx, rc, rc2, dt, hdt, isqrt_dt;
+    double Wc, Fc, W0, Cn, mf, inv_dx3;
+    double rho0, p0, alpha, beta_p;
+    double Ca, Cb, eta, kBT, Ka, Kb;
+    double coeff_c, coeff_d, coeff_r, coeff_t;
+    double g[3], body_amp;
+    int body_axis, split_axis;
+    int filter, clamp, artvis, dem_law, noise;
+    double artvis_rlim, artvis_e;
+    double kn, kt_ratio, zeta, nu_p, E_p, mu_fric;
+    double lub_gap_min, eps_min, Vf;
+    double lever_fluid;
+    uint32_t key0, key1;
+    // float copies for the split-precision pair kernels
+    float rcf, inv_rcf, csf[3], Wcf, Fcf, Caf, Cbf, Kaf, Kbf, isqrt_dtf;
+    float coeff_cf, coeff_df, coeff_rf, coeff_tf, W0f, lever_fluidf;
+    float guard_lo, guard_hi;   // r^2 band re-decided exactly in double
+};
+
+// Device buffers of a context (all device pointers).
+struct Bufs {
+    long long N, Npad;
+    int n_inst, ncell_total, nrigid, cap, K;
+    const Inst *inst;          // [n_inst]
+    // master state (gid order)
+    double *x, *v, *w, *F, *T;
+    int *type, *pinst;
+    double *R, *m, *Iner;               // radius, mass, moment of inertia
+    int *rigid_of;             // gid -> rigid index or -1
+    int *rigid_gid;            // rigid index -> gid
+    // cells
+    const int *cell_rank;      // [ncell_total] linear cell -> Morton rank (within instance)
+    int *key, *slot_in_cell, *ccount, *cstart, *tmp_perm, *perm, *slot_of;
+    int *scan_partials;        // [ceil(ncell_total/1024)+1]
+    // mirrors
+    float4 *A32, *B32, *C32, *D32;
+    double4_32a *A64, *B64, *C64, *D64;
+    int *stype;
+    double *sd, *sp, *sp2;     // density, pressure (raw / filtered) per slot
+    // neighbour list
+    int *nbr, *ncnt;
+    // fluid-particle interaction per rigid index
+    double *eps, *fdg;         // eps [nr], drag [nr][3]
+    double4_32a *rxn;              // per slot: F^DG / S_s (rigid slots only)
+    // DEM history: old / new tables [nr][K]
+    int *h_n, *h_part, *hn_n, *hn_part;
+    double *h_del, *hn_del;
+    // artificial viscosity scratch
+    double *dv;
+    // counters
+    long long *step;
+    int *err;
+    unsigned long long *pair_count;
+    double *probe;             // scratch for probe / diagnostics
+};
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline uint32_t morton_spread(uint32_t v)
+{
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__host__ __device__ inline uint32_t pack_cell(int type, int cx, int cy, int cz)
+{
+    return (uint32_t)type | ((uint32_t)cx << 2) | ((uint32_t)cy << 12) | ((uint32_t)cz << 22);
+}
+
+__device__ __forceinline__ int unpack_type(uint32_t b) { return (int)(b & 3u); }
+__device__ __forceinline__ int unpack_cx(uint32_t b) { return (int)((b >> 2) & 0x3FFu); }
+__device__ __forceinline__ int unpack_cy(uint32_t b) { return (int)((b >> 12) & 0x3FFu); }
+__device__ __forceinline__ int unpack_cz(uint32_t b) { return (int)((b >> 22) & 0x3FFu); }
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor S-box on a 128-bit counter with a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = c.x, b = c.z;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, a), lo0 = 0xD2511F53u * a;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, b), lo1 = 0xCD9E8D57u * b;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Six standard normals of the pair {gi, gj} at `step`: uniforms
+// ((u >> 8) + 1/2) 2^-24 from two Philox blocks, Box-Muller in precision R.
+template <class R> struct Normals;
+
+template <> struct Normals<double> {
+    __device__ __forceinline__ static void gen(uint32_t gi, uint32_t gj, uint32_t step,
+                                               uint32_t k0, uint32_t k1, double z[6])
+    {
+        const uint32_t lo = min(gi, gj), hi = max(gi, gj);
+        const uint4 a = philox4x32_10(make_uint4(lo, hi, step, 0u), k0, k1);
+        const uint4 b = philox4x32_10(make_uint4(lo, hi, step, 1u), k0, k1);
+        const uint32_t u[6] = { a.x, a.y, a.z, a.w, b.x, b.y };
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double U1 = ((double)(u[2 * k] >> 8) + 0.5) * (1.0 / 16777216.0);
+            const double U2 = ((double)(u[2 * k + 1] >> 8) + 0.5) * (1.0 / 16777216.0);
+            const double rad = sqrt(-2.0 * log(U1));
+            double s, c;
+            sincospi(2.0 * U2, &s, &c);
+            z[2 * k] = rad * c;
+            z[2 * k + 1] = rad * s;
+        }
+    }
+};
+
+template <> struct Normals<float> {
+    __device__ __forceinline__ static void gen(uint32_t gi, uint32_t gj, uint32_t step,
+                                               uint32_t k0, uint32_t k1, float z[6])
+    {
+        const uint32_t lo = min(gi, gj), hi = max(gi, gj);
+        const uint4 a = philox4x32_10(make_uint4(lo, hi, step, 0u), k0, k1);
+        const uint4 b = philox4x32_10(make_uint4(lo, hi, step, 1u), k0, k1);
+        const uint32_t u[6] = { a.x, a.y, a.z, a.w, b.x, b.y };
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float U1 = ((float)(u[2 * k] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+            const float U2 = ((float)(u[2 * k + 1] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+            const float rad = sqrtf(-2.0f * logf(U1));
+            float s, c;
+            sincospif(2.0f * U2, &s, &c);
+            z[2 * k] = rad * c;
+            z[2 * k + 1] = rad * s;
+        }
+    }
+};
+
+// ---------------------------------------------------------------- launchers
+// (defined in k_cells.cu, k_pairs.cu, k_update.cu; all enqueue on `st`)
+void launch_cell_keys(const Bufs &b, cudaStream_t st);
+void launch_scan_cells(const Bufs &b, cudaStream_t st);
+void launch_scatter_rank(const Bufs &b, cudaStream_t st);
+void launch_gather(const Bufs &b, int precision, cudaStream_t st);
+void launch_neighbors(const Bufs &b, int precision, cudaStream_t st);
+void launch_density(const Bufs &b, int precision, int any_filter, cudaStream_t st);
+void launch_drag(const Bufs &b, cudaStream_t st);
+void launch_forces(const Bufs &b, int precision, int velver, cudaStream_t st);
+void launch_integrate(const Bufs &b, int precision, int velver, int any_artvis, cudaStream_t st);
+void launch_step_done(const Bufs &b, cudaStream_t st);
+void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long n);
+void launch_diag(const Bufs &b, int inst, cudaStream_t st, long long n);
+void launch_count_pairs(const Bufs &b, cudaStream_t st);
+
+}  // namespace sdpd

@@ -1,0 +1,301 @@
+// k_cells.cu -- compute_neighbor_list (Algorithm 1, Section 3.2) on the GPU.
+//
+// The paper's background grid with linked lists is replaced by a counting
+// sort of the particles into Morton-ranked cells:
+//   K1 cell key per particle + atomic per-cell count      (HBM bound, 1 pass)
+//   K2 exclusive scan of the counts -> cell starts
+//   K3 scatter into cell ranges, K4 rank by gid inside each cell (deterministic
+//      order, so every later sum is reproducible bit for bit)
+//   K5 gather of the cell-sorted mirrors (float4 / double4_32a records)
+//   K6 per particle, the list of neighbours j != i with r_ij < h from the 27
+//      surrounding cells (exact FP64 decision, FP32 prefilter in split mode)
+#include "common.cuh"
+
+namespace sdpd {
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc, bool &out)
+{
+    int k = (int)floor((x - lo) * inv_cs);
+    out = (k < 0) || (k >= nc);
+    return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
+}
+
+__global__ void k_cell_keys(Bufs b)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= b.N) return;
+    const Inst &I = b.inst[b.pinst[g]];
+    int c[3];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        bool o;
+        c[a] = cell_coord(b.x[3 * g + a], I.lo[a], I.inv_cs[a], I.nc[a], o);
+        bad |= o;
+    }
+    if (bad) atomicOr(b.err, ERR_DOMAIN);
+    const int lin = (c[2] * I.nc[1] + c[1]) * I.nc[0] + c[0];
+    const int key = I.cell_base + b.cell_rank[I.cell_base + lin];
+    b.key[g] = key;
+    b.slot_in_cell[g] = atomicAdd(&b.ccount[key], 1);
+}
+
+// --- exclusive scan of the cell counts (three phases, 1024 cells per block)
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) >= o) v += t;
+    }
+    return v;
+}
+
+__device__ int block_excl_scan(int v, int *total)
+{
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = warp_incl_scan(v);
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int s = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
+        s = warp_incl_scan(s);
+        ws[lane] = s;
+    }
+    __syncthreads();
+    const int off = wid ? ws[wid - 1] : 0;
+    *total = ws[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return off + inc - v;
+}
+
+__global__ void k_scan_local(const int *cnt, int *start, int *partials, int n)
+{
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int v = i < n ? cnt[i] : 0;
+    int tot;
+    const int e = block_excl_scan(v, &tot);
+    if (i < n) start[i] = e;
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_partials(int *partials, int nblk)
+{
+    // one block of 1024 threads, sequential over chunks
+    int carry = 0;
+    for (int base = 0; base < nblk; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < nblk ? partials[i] : 0;
+        int tot;
+        const int e = block_excl_scan(v, &tot);
+        if (i < nblk) partials[i] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int *start, const int *partials, int n, long long N)
+{
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) start[i] += partials[blockIdx.x];
+    if (i == 0) start[n] = (int)N;
+}
+
+__global__ void k_scatter(Bufs b)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= b.N) return;
+    b.tmp_perm[b.cstart[b.key[g]] + b.slot_in_cell[g]] = (int)g;
+}
+
+// Rank of each particle among its cell's members by gid (stable, unique).
+__global__ void k_rank(Bufs b)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.N) return;
+    const int g = b.tmp_perm[t];
+    const int c = b.key[g];
+    const int s0 = b.cstart[c], s1 = b.cstart[c + 1];
+    int r = 0;
+    for (int u = s0; u < s1; ++u) r += (b.tmp_perm[u] < g);
+    b.perm[s0 + r] = g;
+    b.slot_of[g] = s0 + r;
+}
+
+// Cell-sorted mirrors for the pair kernels.
+__global__ void k_gather(Bufs b, int precision)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.N) return;
+    const int g = b.perm[s];
+    const int ii = b.pinst[g];
+    const Inst &I = b.inst[ii];
+    const int t = b.type[g];
+    b.stype[s] = t;
+    const double x0 = b.x[3 * g], x1 = b.x[3 * g + 1], x2 = b.x[3 * g + 2];
+    const uint32_t lg = (uint32_t)(g - I.p_begin);
+    if (precision == SDPD_PREC_SPLIT) {
+        int c[3];
+        double xl[3];
+        const double xs[3] = { x0, x1, x2 };
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bool o;
+            c[a] = cell_coord(xs[a], I.lo[a], I.inv_cs[a], I.nc[a], o);
+            xl[a] = xs[a] - (I.lo[a] + (double)c[a] * I.cs[a]);
+        }
+        b.A32[s] = make_float4((float)xl[0], (float)xl[1], (float)xl[2],
+                               __uint_as_float(pack_cell(t, c[0], c[1], c[2])));
+        b.B32[s] = make_float4((float)b.v[3 * g], (float)b.v[3 * g + 1], (float)b.v[3 * g + 2],
+                               (float)b.R[g]);
+        b.C32[s] = make_float4((float)b.w[3 * g], (float)b.w[3 * g + 1], (float)b.w[3 * g + 2],
+                               (float)b.m[g]);
+        b.D32[s].w = __uint_as_float(lg);
+    } else {
+        b.A64[s] = make_double4_32a(x0, x1, x2, (double)t);
+        b.B64[s] = make_double4_32a(b.v[3 * g], b.v[3 * g + 1], b.v[3 * g + 2], b.R[g]);
+        b.C64[s] = make_double4_32a(b.w[3 * g], b.w[3 * g + 1], b.w[3 * g + 2], b.m[g]);
+        b.D64[s].w = (double)lg;
+    }
+}
+
+// The oracle's distance: r = x_i - x_j with the minimum image on periodic
+// axes, r^2 = (x*x + y*y) + z*z, evaluated without fused multiply-adds.
+__device__ __forceinline__ double exact_r2(const double *xi, const double *xj, const Inst &I)
+{
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double t = __dsub_rn(xi[a], xj[a]);
+        if (I.periodic[a]) {
+            const double hL = 0.5 * I.box[a];
+            if (t > hL) t = __dsub_rn(t, I.box[a]);
+            else if (t < -hL) t = __dadd_rn(t, I.box[a]);
+        }
+        d[a] = t;
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+// Neighbour list of particle (slot) s.  Candidates come from the 27 cells
+// around s's cell (cells are at least max(h, largest sphere diameter) wide,
+// periodic axes at least 3 cells).  A pair is listed when r < h, or when both
+// are rigid and r < R_i + R_j (contact only, flagged NB_FAR).
+__global__ void k_neighbors(Bufs b, int precision)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.N) return;
+    const int gi = b.perm[s];
+    const Inst &I = b.inst[b.pinst[gi]];
+    const int ti = b.stype[s];
+    const double xi[3] = { b.x[3 * gi], b.x[3 * gi + 1], b.x[3 * gi + 2] };
+    const double Ri = b.R[gi];
+    int ci[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        bool o;
+        ci[a] = cell_coord(xi[a], I.lo[a], I.inv_cs[a], I.nc[a], o);
+    }
+    float4 Ai = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (precision == SDPD_PREC_SPLIT) Ai = b.A32[s];
+    int cnt = 0;
+    const long long Np = b.Npad;
+    for (int oz = -1; oz <= 1; ++oz) {
+        int cz = ci[2] + oz;
+        if (I.periodic[2]) cz = (cz + I.nc[2]) % I.nc[2];
+        else if (cz < 0 || cz >= I.nc[2]) continue;
+        for (int oy = -1; oy <= 1; ++oy) {
+            int cy = ci[1] + oy;
+            if (I.periodic[1]) cy = (cy + I.nc[1]) % I.nc[1];
+            else if (cy < 0 || cy >= I.nc[1]) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                int cx = ci[0] + ox;
+                if (I.periodic[0]) cx = (cx + I.nc[0]) % I.nc[0];
+                else if (cx < 0 || cx >= I.nc[0]) continue;
+                const int lin = (cz * I.nc[1] + cy) * I.nc[0] + cx;
+                const int key = I.cell_base + b.cell_rank[I.cell_base + lin];
+                const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
+                // shift of the neighbour cell in whole cells (periodic image)
+                const float sx = (float)ox * I.csf[0], sy = (float)oy * I.csf[1],
+                            sz = (float)oz * I.csf[2];
+                for (int j = j0; j < j1; ++j) {
+                    if (j == s) continue;
+                    const int tj = b.stype[j];
+                    const bool both_rigid = (ti == T_RIGID) && (tj == T_RIGID);
+                    int decide;  // 1 in, 0 out, -1 exact test needed
+                    if (precision == SDPD_PREC_SPLIT && !both_rigid) {
+                        const float4 Aj = b.A32[j];
+                        const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy,
+                                    dz = (Ai.z - Aj.z) - sz;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        decide = (r2 < I.guard_lo) ? 1 : ((r2 > I.guard_hi) ? 0 : -1);
+                    } else {
+                        decide = -1;
+                    }
+                    uint32_t entry = (uint32_t)j;
+                    if (decide < 0) {
+                        const int gj = b.perm[j];
+                        const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+                        const double r2 = exact_r2(xi, xj, I);
+                        if (r2 < I.rc2) {
+                            decide = 1;
+                        } else if (both_rigid) {
+                            const double ds = (Ri + b.R[gj]) * (1.0 + 1e-9);
+                            decide = (r2 < ds * ds) ? 1 : 0;
+                            entry |= NB_FAR;
+                        } else {
+                            decide = 0;
+                        }
+                    }
+                    if (decide == 1) {
+                        if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    if (cnt > b.cap) {
+        atomicOr(b.err, ERR_NBR_CAP);
+        cnt = b.cap;
+    }
+    b.ncnt[s] = cnt;
+}
+
+// ---------------------------------------------------------------- launchers
+static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+void launch_cell_keys(const Bufs &b, cudaStream_t st)
+{
+    cudaMemsetAsync(b.ccount, 0, sizeof(int) * (size_t)b.ncell_total, st);
+    if (b.N) k_cell_keys<<<nblk(b.N, 256), 256, 0, st>>>(b);
+}
+
+void launch_scan_cells(const Bufs &b, cudaStream_t st)
+{
+    const int n = b.ncell_total;
+    const int nb = (n + 1023) / 1024;
+    k_scan_local<<<nb, 1024, 0, st>>>(b.ccount, b.cstart, b.scan_partials, n);
+    k_scan_partials<<<1, 1024, 0, st>>>(b.scan_partials, nb);
+    k_scan_add<<<nb, 1024, 0, st>>>(b.cstart, b.scan_partials, n, b.N);
+}
+
+void launch_scatter_rank(const Bufs &b, cudaStream_t st)
+{
+    if (!b.N) return;
+    k_scatter<<<nblk(b.N, 256), 256, 0, st>>>(b);
+    k_rank<<<nblk(b.N, 256), 256, 0, st>>>(b);
+}
+
+void launch_gather(const Bufs &b, int precision, cudaStream_t st)
+{
+    if (b.N) k_gather<<<nblk(b.N, 256), 256, 0, st>>>(b, precision);
+}
+
+void launch_neighbors(const Bufs &b, int precision, cudaStream_t st)
+{
+    if (b.N) k_neighbors<<<nblk(b.N, 128), 128, 0, st>>>(b, precision);
+}
+
+}  // namespace sdpd

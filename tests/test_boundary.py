@@ -1,0 +1,38 @@
+"""The C-ABI library builds (nvcc, sm_103a) and exports every function that
+include/sdpd.h declares.  No compute call: this runs without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2002_03120_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdpd_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared("sdpd.h")
+    for must in ("sdpd_init", "sdpd_build_cells", "sdpd_compute_forces", "sdpd_couple_drag",
+                 "sdpd_integrate", "sdpd_viscosity_probe"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    for header in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        for name in _declared(header):
+            assert hasattr(lib, name), f"{name} declared in {header} but not exported"
+    assert set(binding.EXPORTS) <= set(_declared("sdpd.h"))
+
+
+def test_last_error_callable_without_gpu():
+    lib = binding.load()
+    assert isinstance(lib.sdpd_last_error(), bytes)
