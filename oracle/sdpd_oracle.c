@@ -149,7 +149,8 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 
 /* Six standard normals for the unordered pair {gi, gj} at time step `step`:
  * two Philox blocks (last counter word 0 and 1), uniforms
- * U = ((u >> 8) + 0.5) * 2^-24, Box-Muller on (U0,U1), (U2,U3), (U4,U5). */
+ * U = ((u >> 9) + 0.5) * 2^-23 (24 significant bits: exact in float and
+ * double), Box-Muller on (U0,U1), (U2,U3), (U4,U5). */
 void orc_pair_normals(uint64_t seed, int inst, uint32_t gi, uint32_t gj,
                       long long step, double z[6])
 {
@@ -162,7 +163,7 @@ void orc_pair_normals(uint64_t seed, int inst, uint32_t gi, uint32_t gj,
     }
     double U[6];
     for (int k = 0; k < 6; ++k)
-        U[k] = ((double)(u[k] >> 8) + 0.5) * (1.0 / 16777216.0);
+        U[k] = ((double)(u[k] >> 9) + 0.5) * (1.0 / 8388608.0);
     for (int k = 0; k < 3; ++k) {
         double rad = sqrt(-2.0 * log(U[2 * k]));
         double ang = 2.0 * ORC_PI * U[2 * k + 1];

@@ -267,19 +267,20 @@ sdpd_status prepare(sdpd_ctx *c)
     ALLOC(b.rigid_of, c->N, true);
     if (b.nrigid) CUDA_TRY(cudaMemcpy(b.rigid_gid, rigid_gid.data(), sizeof(int) * b.nrigid, cudaMemcpyHostToDevice));
     if (c->N) CUDA_TRY(cudaMemcpy(b.rigid_of, rigid_of.data(), sizeof(int) * c->N, cudaMemcpyHostToDevice));
-    ALLOC(b.eps, b.nrigid, true);
-    ALLOC(b.fdg, 3 * (size_t)b.nrigid, true);
-    const size_t nk = (size_t)b.nrigid * c->K;
-    ALLOC(b.h_n, b.nrigid, true);
-    ALLOC(b.hn_n, b.nrigid, true);
+    const size_t nr1 = b.nrigid ? (size_t)b.nrigid : 1;
+    ALLOC(b.eps, nr1, true);
+    ALLOC(b.fdg, 3 * nr1, true);
+    const size_t nk = nr1 * c->K;
+    ALLOC(b.h_n, nr1, true);
+    ALLOC(b.hn_n, nr1, true);
     ALLOC(b.h_part, nk, true);
     ALLOC(b.hn_part, nk, true);
     ALLOC(b.h_del, 3 * nk, true);
     ALLOC(b.hn_del, 3 * nk, true);
-    CUDA_TRY(cudaMemset(b.h_n, 0, sizeof(int) * (b.nrigid ? b.nrigid : 1)));
-    CUDA_TRY(cudaMemset(b.hn_n, 0, sizeof(int) * (b.nrigid ? b.nrigid : 1)));
-    CUDA_TRY(cudaMemset(b.eps, 0, sizeof(double) * (b.nrigid ? b.nrigid : 1)));
-    CUDA_TRY(cudaMemset(b.fdg, 0, sizeof(double) * 3 * (b.nrigid ? b.nrigid : 1)));
+    CUDA_TRY(cudaMemset(b.h_n, 0, sizeof(int) * nr1));
+    CUDA_TRY(cudaMemset(b.hn_n, 0, sizeof(int) * nr1));
+    CUDA_TRY(cudaMemset(b.eps, 0, sizeof(double) * nr1));
+    CUDA_TRY(cudaMemset(b.fdg, 0, sizeof(double) * 3 * nr1));
     if (!c->d_inst) {
         sdpd_status s = dalloc(c, &c->d_inst, c->n_inst, false);
         if (s != SDPD_OK) return s;
@@ -544,6 +545,7 @@ sdpd_status sdpd_get_step(sdpd_ctx *c, long long *step)
 sdpd_status sdpd_build_cells(sdpd_ctx *c, void *stream)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    (void)cudaGetLastError();  // launch errors below are this call's own
     sdpd_status s = ensure_geometry(c);
     if (s != SDPD_OK) return s;
     enqueue_build(c, (cudaStream_t)stream);
@@ -556,6 +558,7 @@ sdpd_status sdpd_build_cells(sdpd_ctx *c, void *stream)
 sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->cells_valid) return fail(SDPD_E_STATE, "sdpd_build_cells must precede sdpd_compute_density");
     launch_density(c->b, c->precision, c->any_filter, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
@@ -566,6 +569,7 @@ sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
 sdpd_status sdpd_couple_drag(sdpd_ctx *c, void *stream)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->density_valid) return fail(SDPD_E_STATE, "sdpd_compute_density must precede sdpd_couple_drag");
     launch_drag(c->b, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
@@ -576,6 +580,7 @@ sdpd_status sdpd_couple_drag(sdpd_ctx *c, void *stream)
 sdpd_status sdpd_compute_forces(sdpd_ctx *c, int velver, void *stream)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    (void)cudaGetLastError();  // launch errors below are this call's own
     if (velver != 1 && velver != 2) return fail(SDPD_E_INVALID, "velver must be 1 or 2");
     if (!c->drag_valid) return fail(SDPD_E_STATE, "sdpd_couple_drag must precede sdpd_compute_forces");
     launch_forces(c->b, c->precision, velver, (cudaStream_t)stream);
@@ -586,6 +591,7 @@ sdpd_status sdpd_compute_forces(sdpd_ctx *c, int velver, void *stream)
 sdpd_status sdpd_integrate(sdpd_ctx *c, int velver, void *stream)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    (void)cudaGetLastError();  // launch errors below are this call's own
     if (velver != 1 && velver != 2) return fail(SDPD_E_INVALID, "velver must be 1 or 2");
     if (!c->geometry_ready || !c->b.inst) return fail(SDPD_E_STATE, "no forces computed yet");
     cudaStream_t st = (cudaStream_t)stream;
@@ -603,6 +609,7 @@ sdpd_status sdpd_integrate(sdpd_ctx *c, int velver, void *stream)
 sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    (void)cudaGetLastError();  // launch errors below are this call's own
     if (n_steps < 0) return fail(SDPD_E_INVALID, "negative step count");
     cudaStream_t st = (cudaStream_t)stream;
     sdpd_status s = ensure_geometry(c);

@@ -128,51 +128,46 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Six standard normals of the pair {gi, gj} at `step`: uniforms
-// ((u >> 8) + 1/2) 2^-24 from two Philox blocks, Box-Muller in precision R.
-template <class R> struct Normals;
-
-template <> struct Normals<double> {
-    __device__ __forceinline__ static void gen(uint32_t gi, uint32_t gj, uint32_t step,
-                                               uint32_t k0, uint32_t k1, double z[6])
+// Six standard normals of the pair {gi, gj} at `step`: two Philox blocks,
+// uniforms ((u >> 9) + 1/2) 2^-23 (exact in float and double), Box-Muller on
+// (u0,u1), (u2,u3), (u4,u5) in precision R.  Scalars only (no local arrays).
+template <class R> struct BoxMuller;
+template <> struct BoxMuller<double> {
+    __device__ __forceinline__ static void pair(uint32_t ua, uint32_t ub, double &z0, double &z1)
     {
-        const uint32_t lo = min(gi, gj), hi = max(gi, gj);
-        const uint4 a = philox4x32_10(make_uint4(lo, hi, step, 0u), k0, k1);
-        const uint4 b = philox4x32_10(make_uint4(lo, hi, step, 1u), k0, k1);
-        const uint32_t u[6] = { a.x, a.y, a.z, a.w, b.x, b.y };
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const double U1 = ((double)(u[2 * k] >> 8) + 0.5) * (1.0 / 16777216.0);
-            const double U2 = ((double)(u[2 * k + 1] >> 8) + 0.5) * (1.0 / 16777216.0);
-            const double rad = sqrt(-2.0 * log(U1));
-            double s, c;
-            sincospi(2.0 * U2, &s, &c);
-            z[2 * k] = rad * c;
-            z[2 * k + 1] = rad * s;
-        }
+        const double U1 = ((double)(ua >> 9) + 0.5) * (1.0 / 8388608.0);
+        const double U2 = ((double)(ub >> 9) + 0.5) * (1.0 / 8388608.0);
+        const double rad = sqrt(-2.0 * log(U1));
+        double s, c;
+        sincospi(2.0 * U2, &s, &c);
+        z0 = rad * c;
+        z1 = rad * s;
+    }
+};
+template <> struct BoxMuller<float> {
+    __device__ __forceinline__ static void pair(uint32_t ua, uint32_t ub, float &z0, float &z1)
+    {
+        const float U1 = ((float)(ua >> 9) + 0.5f) * (1.0f / 8388608.0f);
+        const float U2 = ((float)(ub >> 9) + 0.5f) * (1.0f / 8388608.0f);
+        const float rad = sqrtf(-2.0f * logf(U1));
+        float s, c;
+        sincospif(2.0f * U2, &s, &c);
+        z0 = rad * c;
+        z1 = rad * s;
     }
 };
 
-template <> struct Normals<float> {
-    __device__ __forceinline__ static void gen(uint32_t gi, uint32_t gj, uint32_t step,
-                                               uint32_t k0, uint32_t k1, float z[6])
-    {
-        const uint32_t lo = min(gi, gj), hi = max(gi, gj);
-        const uint4 a = philox4x32_10(make_uint4(lo, hi, step, 0u), k0, k1);
-        const uint4 b = philox4x32_10(make_uint4(lo, hi, step, 1u), k0, k1);
-        const uint32_t u[6] = { a.x, a.y, a.z, a.w, b.x, b.y };
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float U1 = ((float)(u[2 * k] >> 8) + 0.5f) * (1.0f / 16777216.0f);
-            const float U2 = ((float)(u[2 * k + 1] >> 8) + 0.5f) * (1.0f / 16777216.0f);
-            const float rad = sqrtf(-2.0f * logf(U1));
-            float s, c;
-            sincospif(2.0f * U2, &s, &c);
-            z[2 * k] = rad * c;
-            z[2 * k + 1] = rad * s;
-        }
-    }
-};
+template <class R>
+__device__ __forceinline__ void pair_normals(uint32_t gi, uint32_t gj, uint32_t step, uint32_t k0,
+                                             uint32_t k1, R &z0, R &z1, R &z2, R &z3, R &z4, R &z5)
+{
+    const uint32_t lo = min(gi, gj), hi = max(gi, gj);
+    const uint4 a = philox4x32_10(make_uint4(lo, hi, step, 0u), k0, k1);
+    const uint4 b = philox4x32_10(make_uint4(lo, hi, step, 1u), k0, k1);
+    BoxMuller<R>::pair(a.x, a.y, z0, z1);
+    BoxMuller<R>::pair(a.z, a.w, z2, z3);
+    BoxMuller<R>::pair(b.x, b.y, z4, z5);
+}
 
 // ---------------------------------------------------------------- launchers
 // (defined in k_cells.cu, k_pairs.cu, k_update.cu; all enqueue on `st`)
