@@ -193,6 +193,13 @@ sdpd_status sdpd_count_pairs(sdpd_ctx *ctx, long long *n_pairs);
  * out[8] number of non-finite values in x, v, w. */
 sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
 
+/* Force-pass variant: newton3 = 1 (default) evaluates each unordered pair once
+ * (the lower slot owns it, its result goes to the partner through a pair
+ * buffer; deterministic, no atomics); newton3 = 0 evaluates every pair from
+ * both sides.  Both give the same forces up to summation order.  Invalidates
+ * the current neighbour build and graph.  Synchronous. */
+sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
+
 /* Number of kernel nodes in the captured one-step graph of sdpd_step (0 if
  * sdpd_step has not run yet).  Synchronous. */
 sdpd_status sdpd_graph_kernels(sdpd_ctx *ctx, long long *n_kernels);

@@ -50,6 +50,7 @@ struct sdpd_ctx {
     std::vector<void *> geo_allocs;    // buffers sized by the grid / rigid count
     Inst *d_inst = nullptr;
     int any_filter = 0, any_artvis = 0;
+    int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
     int sticky_err = 0;
     long long host_step = 0;
@@ -242,6 +243,7 @@ sdpd_status prepare(sdpd_ctx *c)
         I.lever_fluidf = (float)I.lever_fluid;
         I.guard_lo = (float)(I.rc2 * (1.0 - 1e-5));
         I.guard_hi = (float)(I.rc2 * (1.0 + 1e-5));
+        I.artvis_r2f_hi = (float)(I.artvis_rlim * I.artvis_rlim * (1.0 + 1e-5));
     }
     Bufs &b = c->b;
     b.ncell_total = cell_base;
@@ -249,6 +251,43 @@ sdpd_status prepare(sdpd_ctx *c)
     ALLOC(rank_d, cell_base, true);
     CUDA_TRY(cudaMemcpy(rank_d, rank_all.data(), sizeof(int) * cell_base, cudaMemcpyHostToDevice));
     b.cell_rank = rank_d;
+    // neighbour cells of every cell, ascending key, with the offset code
+    // (ox+1) + 3 (oy+1) + 9 (oz+1): neighbour lists then come out sorted by slot
+    {
+        std::vector<int> adj((size_t)cell_base * 27, -1);
+        for (int k = 0; k < c->n_inst; ++k) {
+            const Inst &I = c->inst[k];
+            for (int z = 0; z < I.nc[2]; ++z)
+                for (int y = 0; y < I.nc[1]; ++y)
+                    for (int x = 0; x < I.nc[0]; ++x) {
+                        const int lin = (z * I.nc[1] + y) * I.nc[0] + x;
+                        const int key = I.cell_base + rank_all[I.cell_base + lin];
+                        std::vector<std::pair<int, int>> nbs;
+                        for (int oz = -1; oz <= 1; ++oz)
+                            for (int oy = -1; oy <= 1; ++oy)
+                                for (int ox = -1; ox <= 1; ++ox) {
+                                    int cc[3] = { x + ox, y + oy, z + oz };
+                                    bool ok = true;
+                                    for (int a = 0; a < 3; ++a) {
+                                        if (I.periodic[a]) cc[a] = (cc[a] + I.nc[a]) % I.nc[a];
+                                        else if (cc[a] < 0 || cc[a] >= I.nc[a]) ok = false;
+                                    }
+                                    if (!ok) continue;
+                                    const int l2 = (cc[2] * I.nc[1] + cc[1]) * I.nc[0] + cc[0];
+                                    const int k2 = I.cell_base + rank_all[I.cell_base + l2];
+                                    nbs.push_back({ k2, (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1) });
+                                }
+                        std::sort(nbs.begin(), nbs.end());
+                        for (size_t q = 0; q < nbs.size(); ++q)
+                            adj[(size_t)key * 27 + q] = (nbs[q].first << 5) | nbs[q].second;
+                    }
+        }
+        if (cell_base >= (1 << 26)) return fail(SDPD_E_INVALID, "too many cells");
+        int *adj_d = nullptr;
+        ALLOC(adj_d, adj.size(), true);
+        CUDA_TRY(cudaMemcpy(adj_d, adj.data(), sizeof(int) * adj.size(), cudaMemcpyHostToDevice));
+        b.cell_adj = adj_d;
+    }
     ALLOC(b.ccount, cell_base, true);
     ALLOC(b.cstart, cell_base + 1, true);
     ALLOC(b.scan_partials, (cell_base + 1023) / 1024 + 1, true);
@@ -308,6 +347,8 @@ sdpd_status check_err(sdpd_ctx *c)
     if (e & ERR_NBR_CAP) return fail(SDPD_E_CAPACITY, "neighbour list capacity exceeded (raise max_neighbors)");
     if (e & ERR_CONTACT_CAP) return fail(SDPD_E_CAPACITY, "contact history capacity exceeded (raise max_contacts)");
     if (e & ERR_CELL_CAP) return fail(SDPD_E_CAPACITY, "cell capacity exceeded");
+    if (e & ERR_PAIR_CAP) return fail(SDPD_E_CAPACITY, "pair buffer capacity exceeded");
+    if (e & ERR_REV) return fail(SDPD_E_STATE, "neighbour lists not symmetric");
     if (e & ERR_NONFINITE) return fail(SDPD_E_NONFINITE, "non-finite position, velocity or spin");
     if (e & ERR_DOMAIN) return fail(SDPD_E_DOMAIN, "particle outside the grid on a wall axis");
     return fail(SDPD_E_CUDA, "unknown device error");
@@ -325,7 +366,7 @@ void enqueue_build(sdpd_ctx *c, cudaStream_t st)
     launch_scan_cells(c->b, st);
     launch_scatter_rank(c->b, st);
     launch_gather(c->b, c->precision, st);
-    launch_neighbors(c->b, c->precision, st);
+    launch_neighbors(c->b, c->precision, c->newton3, st);
 }
 
 }  // namespace
@@ -393,13 +434,26 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     IALLOC(b.slot_of, N); IALLOC(b.stype, N);
     IALLOC(b.sd, N); IALLOC(b.sp, N); IALLOC(b.sp2, N);
     IALLOC(b.rxn, N);
+    IALLOC(b.A32, N);
     if (precision == SDPD_PREC_SPLIT) {
-        IALLOC(b.A32, N); IALLOC(b.B32, N); IALLOC(b.C32, N); IALLOC(b.D32, N);
+        IALLOC(b.B32, N); IALLOC(b.C32, N); IALLOC(b.D32, N);
     } else {
         IALLOC(b.A64, N); IALLOC(b.B64, N); IALLOC(b.C64, N); IALLOC(b.D64, N);
     }
     IALLOC(b.nbr, (size_t)c->cap * c->Npad);
     IALLOC(b.ncnt, N);
+    IALLOC(b.nfirst, N);
+    IALLOC(b.rev, (size_t)c->cap * c->Npad);
+    b.capown = c->cap;
+    {
+        const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
+        char *pa = nullptr, *pb = nullptr, *oa = nullptr, *ob = nullptr;
+        IALLOC(pa, 4 * rs * (size_t)c->cap * c->Npad);
+        IALLOC(pb, 2 * rs * (size_t)c->cap * c->Npad);
+        IALLOC(oa, 4 * rs * (size_t)N);
+        IALLOC(ob, 2 * rs * (size_t)N);
+        b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;
+    }
     IALLOC(b.step, 1); IALLOC(b.err, 1); IALLOC(b.pair_count, 1);
     IALLOC(b.probe, 4096 * 2 + 64);
 #undef IALLOC
@@ -583,7 +637,7 @@ sdpd_status sdpd_compute_forces(sdpd_ctx *c, int velver, void *stream)
     (void)cudaGetLastError();  // launch errors below are this call's own
     if (velver != 1 && velver != 2) return fail(SDPD_E_INVALID, "velver must be 1 or 2");
     if (!c->drag_valid) return fail(SDPD_E_STATE, "sdpd_couple_drag must precede sdpd_compute_forces");
-    launch_forces(c->b, c->precision, velver, (cudaStream_t)stream);
+    launch_forces(c->b, c->precision, velver, c->newton3, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     return SDPD_OK;
 }
@@ -631,12 +685,12 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaStream_t cs = c->cap_stream;
         launch_drag(c->b, cs);
-        launch_forces(c->b, c->precision, 1, cs);
+        launch_forces(c->b, c->precision, 1, c->newton3, cs);
         launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
         enqueue_build(c, cs);
         launch_density(c->b, c->precision, c->any_filter, cs);
         launch_drag(c->b, cs);
-        launch_forces(c->b, c->precision, 2, cs);
+        launch_forces(c->b, c->precision, 2, c->newton3, cs);
         launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);
         launch_step_done(c->b, cs);
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &c->graph_def);
@@ -650,6 +704,19 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
     c->cells_valid = c->density_valid = true;
     c->drag_valid = false;
     return check_err(c);
+}
+
+sdpd_status sdpd_set_force_mode(sdpd_ctx *c, int newton3)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (newton3 != 0 && newton3 != 1) return fail(SDPD_E_INVALID, "newton3 must be 0 or 1");
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (newton3 != c->newton3) {
+        c->newton3 = newton3;
+        drop_graph(c);
+        c->cells_valid = c->density_valid = c->drag_valid = false;
+    }
+    return SDPD_OK;
 }
 
 sdpd_status sdpd_graph_kernels(sdpd_ctx *c, long long *n_kernels)

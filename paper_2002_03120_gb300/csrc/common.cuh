@@ -23,7 +23,7 @@ constexpr double PI = 3.14159265358979323846;
 
 // device error word bits
 constexpr int ERR_NBR_CAP = 1, ERR_CELL_CAP = 2, ERR_CONTACT_CAP = 4, ERR_NONFINITE = 8,
-              ERR_DOMAIN = 16;
+              ERR_DOMAIN = 16, ERR_PAIR_CAP = 32, ERR_REV = 64;
 
 // rigid-pair list entries beyond h (contact only) carry this flag
 constexpr uint32_t NB_FAR = 0x80000000u;
@@ -52,6 +52,7 @@ struct Inst {
     float rcf, inv_rcf, csf[3], Wcf, Fcf, Caf, Cbf, Kaf, Kbf, isqrt_dtf;
     float coeff_cf, coeff_df, coeff_rf, coeff_tf, W0f, lever_fluidf;
     float guard_lo, guard_hi;   // r^2 band re-decided exactly in double
+    float artvis_r2f_hi;        // collision pass: float prefilter bound
 };
 
 // Device buffers of a context (all device pointers).
@@ -67,6 +68,7 @@ struct Bufs {
     int *rigid_gid;            // rigid index -> gid
     // cells
     const int *cell_rank;      // [ncell_total] linear cell -> Morton rank (within instance)
+    const int *cell_adj;       // [ncell_total][27] (key << 5 | offset code), ascending key, -1 = none
     int *key, *slot_in_cell, *ccount, *cstart, *tmp_perm, *perm, *slot_of;
     int *scan_partials;        // [ceil(ncell_total/1024)+1]
     // mirrors
@@ -74,8 +76,14 @@ struct Bufs {
     double4_32a *A64, *B64, *C64, *D64;
     int *stype;
     double *sd, *sp, *sp2;     // density, pressure (raw / filtered) per slot
-    // neighbour list
-    int *nbr, *ncnt;
+    // neighbour list (each list ascending in slot); nfirst = entries below the
+    // particle's own slot; rev = position of the pair in the lower partner's
+    // owned part (Newton-3 pass)
+    int *nbr, *ncnt, *nfirst;
+    uint16_t *rev;
+    int capown;                // owned entries per particle in the pair buffer
+    void *resA, *resB;         // pair results [capown][Npad]: R4 {f, t.x}, R2 {t.y, t.z}
+    void *ownA, *ownB;         // per slot sums of the owned pairs
     // fluid-particle interaction per rigid index
     double *eps, *fdg;         // eps [nr], drag [nr][3]
     double4_32a *rxn;              // per slot: F^DG / S_s (rigid slots only)
@@ -169,16 +177,68 @@ __device__ __forceinline__ void pair_normals(uint32_t gi, uint32_t gj, uint32_t 
     BoxMuller<R>::pair(b.x, b.y, z4, z5);
 }
 
+// Geometry constants of an instance held in registers for the pair loop.
+template <class R> struct Geo;
+template <> struct Geo<float> {
+    bool p0, p1, p2;
+    int n0, n1, n2;
+    float c0, c1, c2;
+    __device__ __forceinline__ explicit Geo(const Inst &I)
+        : p0(I.periodic[0]), p1(I.periodic[1]), p2(I.periodic[2]), n0(I.nc[0]), n1(I.nc[1]),
+          n2(I.nc[2]), c0(I.csf[0]), c1(I.csf[1]), c2(I.csf[2]) {}
+    __device__ __forceinline__ void disp(const float4 &Ai, const float4 &Aj, float &rx, float &ry,
+                                         float &rz) const
+    {
+        const uint32_t bi = __float_as_uint(Ai.w), bj = __float_as_uint(Aj.w);
+        int d0 = unpack_cx(bi) - unpack_cx(bj), d1 = unpack_cy(bi) - unpack_cy(bj),
+            d2 = unpack_cz(bi) - unpack_cz(bj);
+        if (p0) d0 = d0 > 1 ? d0 - n0 : (d0 < -1 ? d0 + n0 : d0);
+        if (p1) d1 = d1 > 1 ? d1 - n1 : (d1 < -1 ? d1 + n1 : d1);
+        if (p2) d2 = d2 > 1 ? d2 - n2 : (d2 < -1 ? d2 + n2 : d2);
+        rx = (Ai.x - Aj.x) + (float)d0 * c0;
+        ry = (Ai.y - Aj.y) + (float)d1 * c1;
+        rz = (Ai.z - Aj.z) + (float)d2 * c2;
+    }
+};
+template <> struct Geo<double> {
+    bool p0, p1, p2;
+    double L0, L1, L2;
+    __device__ __forceinline__ explicit Geo(const Inst &I)
+        : p0(I.periodic[0]), p1(I.periodic[1]), p2(I.periodic[2]), L0(I.box[0]), L1(I.box[1]),
+          L2(I.box[2]) {}
+    __device__ __forceinline__ static double img(double d, bool p, double L)
+    {
+        if (!p) return d;
+        const double h = 0.5 * L;
+        return d > h ? d - L : (d < -h ? d + L : d);
+    }
+    __device__ __forceinline__ void disp(const double4_32a &Ai, const double4_32a &Aj, double &rx,
+                                         double &ry, double &rz) const
+    {
+        rx = img(Ai.x - Aj.x, p0, L0);
+        ry = img(Ai.y - Aj.y, p1, L1);
+        rz = img(Ai.z - Aj.z, p2, L2);
+    }
+};
+
+// Warp sum (butterfly: every lane ends with the same, order-fixed result).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // ---------------------------------------------------------------- launchers
 // (defined in k_cells.cu, k_pairs.cu, k_update.cu; all enqueue on `st`)
 void launch_cell_keys(const Bufs &b, cudaStream_t st);
 void launch_scan_cells(const Bufs &b, cudaStream_t st);
 void launch_scatter_rank(const Bufs &b, cudaStream_t st);
 void launch_gather(const Bufs &b, int precision, cudaStream_t st);
-void launch_neighbors(const Bufs &b, int precision, cudaStream_t st);
+void launch_neighbors(const Bufs &b, int precision, int need_rev, cudaStream_t st);
 void launch_density(const Bufs &b, int precision, int any_filter, cudaStream_t st);
 void launch_drag(const Bufs &b, cudaStream_t st);
-void launch_forces(const Bufs &b, int precision, int velver, cudaStream_t st);
+void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st);
 void launch_integrate(const Bufs &b, int precision, int velver, int any_artvis, cudaStream_t st);
 void launch_step_done(const Bufs &b, cudaStream_t st);
 void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long n);

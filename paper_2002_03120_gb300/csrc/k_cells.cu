@@ -135,7 +135,9 @@ __global__ void k_gather(Bufs b, int precision)
     b.stype[s] = t;
     const double x0 = b.x[3 * g], x1 = b.x[3 * g + 1], x2 = b.x[3 * g + 2];
     const uint32_t lg = (uint32_t)(g - I.p_begin);
-    if (precision == SDPD_PREC_SPLIT) {
+    {
+        // cell-relative float coordinates (both precisions: the neighbour
+        // search and the collision pass prefilter on them)
         int c[3];
         double xl[3];
         const double xs[3] = { x0, x1, x2 };
@@ -147,6 +149,8 @@ __global__ void k_gather(Bufs b, int precision)
         }
         b.A32[s] = make_float4((float)xl[0], (float)xl[1], (float)xl[2],
                                __uint_as_float(pack_cell(t, c[0], c[1], c[2])));
+    }
+    if (precision == SDPD_PREC_SPLIT) {
         b.B32[s] = make_float4((float)b.v[3 * g], (float)b.v[3 * g + 1], (float)b.v[3 * g + 2],
                                (float)b.R[g]);
         b.C32[s] = make_float4((float)b.w[3 * g], (float)b.w[3 * g + 1], (float)b.w[3 * g + 2],
@@ -190,77 +194,91 @@ __global__ void k_neighbors(Bufs b, int precision)
     const Inst &I = b.inst[b.pinst[gi]];
     const int ti = b.stype[s];
     const double xi[3] = { b.x[3 * gi], b.x[3 * gi + 1], b.x[3 * gi + 2] };
-    const double Ri = b.R[gi];
+    const double Ri = (ti == T_RIGID) ? b.R[gi] : 0.0;
     int ci[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         bool o;
         ci[a] = cell_coord(xi[a], I.lo[a], I.inv_cs[a], I.nc[a], o);
     }
-    float4 Ai = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (precision == SDPD_PREC_SPLIT) Ai = b.A32[s];
-    int cnt = 0;
+    const float4 Ai = b.A32[s];
+    const float glo = I.guard_lo, ghi = I.guard_hi;
+    const int key_i = I.cell_base + b.cell_rank[I.cell_base + (ci[2] * I.nc[1] + ci[1]) * I.nc[0] + ci[0]];
+    const int *adj = b.cell_adj + (long long)key_i * 27;
+    int cnt = 0, nlow = 0;
     const long long Np = b.Npad;
-    for (int oz = -1; oz <= 1; ++oz) {
-        int cz = ci[2] + oz;
-        if (I.periodic[2]) cz = (cz + I.nc[2]) % I.nc[2];
-        else if (cz < 0 || cz >= I.nc[2]) continue;
-        for (int oy = -1; oy <= 1; ++oy) {
-            int cy = ci[1] + oy;
-            if (I.periodic[1]) cy = (cy + I.nc[1]) % I.nc[1];
-            else if (cy < 0 || cy >= I.nc[1]) continue;
-            for (int ox = -1; ox <= 1; ++ox) {
-                int cx = ci[0] + ox;
-                if (I.periodic[0]) cx = (cx + I.nc[0]) % I.nc[0];
-                else if (cx < 0 || cx >= I.nc[0]) continue;
-                const int lin = (cz * I.nc[1] + cy) * I.nc[0] + cx;
-                const int key = I.cell_base + b.cell_rank[I.cell_base + lin];
-                const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
-                // shift of the neighbour cell in whole cells (periodic image)
-                const float sx = (float)ox * I.csf[0], sy = (float)oy * I.csf[1],
-                            sz = (float)oz * I.csf[2];
-                for (int j = j0; j < j1; ++j) {
-                    if (j == s) continue;
-                    const int tj = b.stype[j];
-                    const bool both_rigid = (ti == T_RIGID) && (tj == T_RIGID);
-                    int decide;  // 1 in, 0 out, -1 exact test needed
-                    if (precision == SDPD_PREC_SPLIT && !both_rigid) {
-                        const float4 Aj = b.A32[j];
-                        const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy,
-                                    dz = (Ai.z - Aj.z) - sz;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        decide = (r2 < I.guard_lo) ? 1 : ((r2 > I.guard_hi) ? 0 : -1);
-                    } else {
-                        decide = -1;
-                    }
-                    uint32_t entry = (uint32_t)j;
-                    if (decide < 0) {
-                        const int gj = b.perm[j];
-                        const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-                        const double r2 = exact_r2(xi, xj, I);
-                        if (r2 < I.rc2) {
-                            decide = 1;
-                        } else if (both_rigid) {
-                            const double ds = (Ri + b.R[gj]) * (1.0 + 1e-9);
-                            decide = (r2 < ds * ds) ? 1 : 0;
-                            entry |= NB_FAR;
-                        } else {
-                            decide = 0;
-                        }
-                    }
-                    if (decide == 1) {
-                        if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
-                        ++cnt;
-                    }
+    // neighbour cells in ascending key order: the list comes out sorted by slot
+    for (int q = 0; q < 27; ++q) {
+        const int code = adj[q];
+        if (code < 0) break;
+        const int key = code >> 5, oc = code & 31;
+        const int ox = oc % 3 - 1, oy = (oc / 3) % 3 - 1, oz = oc / 9 - 1;
+        const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
+        // shift of the neighbour cell in whole cells (periodic image)
+        const float sx = (float)ox * I.csf[0], sy = (float)oy * I.csf[1], sz = (float)oz * I.csf[2];
+        for (int j = j0; j < j1; ++j) {
+            if (j == s) continue;
+            const float4 Aj = b.A32[j];
+            const int tj = unpack_type(__float_as_uint(Aj.w));
+            const bool both_rigid = (ti == T_RIGID) && (tj == T_RIGID);
+            const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy, dz = (Ai.z - Aj.z) - sz;
+            const float r2f = dx * dx + dy * dy + dz * dz;
+            // 1 in, 0 out, -1: inside the guard band, decide exactly
+            int decide = both_rigid ? -1 : ((r2f < glo) ? 1 : ((r2f > ghi) ? 0 : -1));
+            uint32_t entry = (uint32_t)j;
+            if (decide < 0) {
+                const int gj = b.perm[j];
+                const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+                const double r2 = exact_r2(xi, xj, I);
+                if (r2 < I.rc2) {
+                    decide = 1;
+                } else if (both_rigid) {
+                    const double ds = (Ri + b.R[gj]) * (1.0 + 1e-9);
+                    decide = (r2 < ds * ds) ? 1 : 0;
+                    entry |= NB_FAR;
+                } else {
+                    decide = 0;
                 }
+            }
+            if (decide == 1) {
+                if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
+                ++cnt;
+                nlow += (j < s);
             }
         }
     }
+    b.nfirst[s] = nlow < b.cap ? nlow : b.cap;
     if (cnt > b.cap) {
         atomicOr(b.err, ERR_NBR_CAP);
         cnt = b.cap;
     }
     b.ncnt[s] = cnt;
+}
+
+// For every entry of s's list below s (partner i < s), the position of s in
+// the owned (upper) part of i's list, found by binary search (lists are
+// ascending).  The Newton-3 force pass reads the pair result from there.
+__global__ void k_rev(Bufs b)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.N) return;
+    const long long Np = b.Npad;
+    const int first = b.nfirst[s];
+    if (b.ncnt[s] - first > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+    for (int k = 0; k < first; ++k) {
+        const int i = (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR);
+        int lo = b.nfirst[i], hi = b.ncnt[i];
+        const int f0 = lo;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int v = (int)((uint32_t)b.nbr[(long long)mid * Np + i] & ~NB_FAR);
+            if (v < s) lo = mid + 1;
+            else hi = mid;
+        }
+        const bool ok = lo < b.ncnt[i] && (int)((uint32_t)b.nbr[(long long)lo * Np + i] & ~NB_FAR) == (int)s;
+        if (!ok) atomicOr(b.err, ERR_REV);
+        b.rev[(long long)k * Np + s] = (uint16_t)(ok ? lo - f0 : 0);
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -293,9 +311,11 @@ void launch_gather(const Bufs &b, int precision, cudaStream_t st)
     if (b.N) k_gather<<<nblk(b.N, 256), 256, 0, st>>>(b, precision);
 }
 
-void launch_neighbors(const Bufs &b, int precision, cudaStream_t st)
+void launch_neighbors(const Bufs &b, int precision, int need_rev, cudaStream_t st)
 {
-    if (b.N) k_neighbors<<<nblk(b.N, 128), 128, 0, st>>>(b, precision);
+    if (!b.N) return;
+    k_neighbors<<<nblk(b.N, 128), 128, 0, st>>>(b, precision);
+    if (need_rev) k_rev<<<nblk(b.N, 128), 128, 0, st>>>(b);
 }
 
 }  // namespace sdpd

@@ -94,9 +94,17 @@ __global__ void k_artvis(Bufs b)
         const double vi[3] = { b.v[3 * g], b.v[3 * g + 1], b.v[3 * g + 2] };
         const double mi = b.m[g];
         const int n = b.ncnt[s];
+        const Geo<float> geo(I);
+        const float4 Ai = b.A32[s];
+        const float r2hi = I.artvis_r2f_hi;
         for (int k = 0; k < n; ++k) {
             const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
             if (e & NB_FAR) continue;
+            // float prefilter on the cell-relative mirror; exact test below
+            const float4 Aj = b.A32[e];
+            float fx, fy, fz;
+            geo.disp(Ai, Aj, fx, fy, fz);
+            if (fx * fx + fy * fy + fz * fz > r2hi) continue;
             const int gj = b.perm[e];
             const int tj = b.type[gj];
             if (tj != T_FLUID && tj != T_RIGID) continue;

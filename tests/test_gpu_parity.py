@@ -180,20 +180,31 @@ def test_deterministic(precision):
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_batched_equals_single_and_oracle(precision):
-    insts = [CASES["periodic12"], CASES["sediment_small"], CASES["slurry_small"]]
-    multi = B.Sim(insts, precision=precision)
+    # Instances of one context are independent: with the noise off (its key
+    # carries the instance number) every instance reproduces its own
+    # single-instance context bit for bit; with the noise on, each matches the
+    # oracle keyed with the same instance number.
+    quiet = [dict(c, params=dict(c["params"], coeff_t=0.0))
+             for c in (CASES["periodic12"], CASES["sediment_small"], CASES["slurry_small"])]
+    multi = B.Sim(quiet, precision=precision)
     multi.step_count = 2
     multi.evaluate(1)
-    for k, case in enumerate(insts):
+    for k, case in enumerate(quiet):
         single = _gpu_eval(case, precision, step=2)
         a, b = multi.state(k), single.state()
         assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["N"], b["N"])
         single.close()
-    # instance 1 against the oracle, whose noise key carries instance id 1
-    orc = oracle.OracleSim(insts[1], inst=1)
-    orc.step = 2
-    orc.evaluate(1)
-    assert rel_l2(multi.state(1)["F"], orc.state()["F"]) < TOL_FORCE[precision]
+    noisy = [CASES["periodic12"], CASES["sediment_small"], CASES["slurry_small"]]
+    multi = B.Sim(noisy, precision=precision)
+    multi.step_count = 2
+    multi.evaluate(1)
+    for k, case in enumerate(noisy):
+        orc = oracle.OracleSim(case, inst=k)
+        orc.step = 2
+        orc.evaluate(1)
+        o = orc.state()
+        assert rel_l2(multi.state(k)["F"], o["F"]) < TOL_FORCE[precision]
+        assert rel_l2(multi.state(k)["N"], o["N"]) < TOL_FORCE[precision]
 
 
 def test_momentum_conserved_over_steps():
@@ -249,3 +260,22 @@ def test_stage_order_enforced():
     with pytest.raises(B.SdpdError) as e:
         sim.compute_forces(1)
     assert e.value.code == 8
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("name", ["config1_8192", "sediment_small", "dambreak_small"])
+def test_newton3_equals_direct(name, precision):
+    # the half-pair pass evaluates each unordered pair once; the direct pass
+    # from both sides: same forces up to summation order
+    case = CASES[name]
+    a = _gpu_eval(case, precision, step=4)
+    b = B.Sim(case, precision=precision)
+    b.set_force_mode(0)
+    b.step_count = 4
+    b.evaluate(1)
+    sa, sb = a.state(), b.state()
+    tol = 1e-12 if precision == B.SDPD_PREC_FP64 else 2e-5
+    assert rel_l2(sa["F"], sb["F"]) < tol
+    assert rel_l2(sa["N"], sb["N"]) < tol
+    orc = _oracle_eval(case, step=4)
+    assert rel_l2(sb["F"], orc.state()["F"]) < TOL_FORCE[precision]
