@@ -206,6 +206,7 @@ __global__ void k_neighbors(Bufs b, int precision)
     const int key_i = I.cell_base + b.cell_rank[I.cell_base + (ci[2] * I.nc[1] + ci[1]) * I.nc[0] + ci[0]];
     const int *adj = b.cell_adj + (long long)key_i * 27;
     int cnt = 0, nlow = 0;
+    bool rig = false;
     const long long Np = b.Npad;
     // neighbour cells in ascending key order: the list comes out sorted by slot
     for (int q = 0; q < 27; ++q) {
@@ -244,10 +245,12 @@ __global__ void k_neighbors(Bufs b, int precision)
                 if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
                 ++cnt;
                 nlow += (j < s);
+                rig |= (tj == T_RIGID);
             }
         }
     }
     b.nfirst[s] = nlow < b.cap ? nlow : b.cap;
+    b.nbflag[s] = rig ? 1 : 0;
     if (cnt > b.cap) {
         atomicOr(b.err, ERR_NBR_CAP);
         cnt = b.cap;
@@ -255,29 +258,36 @@ __global__ void k_neighbors(Bufs b, int precision)
     b.ncnt[s] = cnt;
 }
 
-// For every entry of s's list below s (partner i < s), the position of s in
-// the owned (upper) part of i's list, found by binary search (lists are
-// ascending).  The Newton-3 force pass reads the pair result from there.
+// For every owned entry of s (partner j > s), the position of s in the lower
+// part of j's list.  Lists are ascending, and consecutive partners of s are
+// mostly neighbours of each other, so the search walks from the previous
+// answer instead of bisecting.  The Newton-3 force pass writes the partner's
+// share of each pair result there.
 __global__ void k_rev(Bufs b)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const long long Np = b.Npad;
-    const int first = b.nfirst[s];
-    if (b.ncnt[s] - first > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
-    for (int k = 0; k < first; ++k) {
-        const int i = (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR);
-        int lo = b.nfirst[i], hi = b.ncnt[i];
-        const int f0 = lo;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const int v = (int)((uint32_t)b.nbr[(long long)mid * Np + i] & ~NB_FAR);
-            if (v < s) lo = mid + 1;
-            else hi = mid;
+    const int first = b.nfirst[s], n = b.ncnt[s];
+    int p = 0;
+    for (int k = first; k < n; ++k) {
+        const int j = (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR);
+        const int lim = b.nfirst[j];
+        if (p >= lim) p = lim - 1;
+        if (p < 0) p = 0;
+        const int *col = b.nbr + j;
+        int v = lim > 0 ? (int)((uint32_t)col[(long long)p * Np] & ~NB_FAR) : -1;
+        while (v < (int)s && p + 1 < lim) {
+            ++p;
+            v = (int)((uint32_t)col[(long long)p * Np] & ~NB_FAR);
         }
-        const bool ok = lo < b.ncnt[i] && (int)((uint32_t)b.nbr[(long long)lo * Np + i] & ~NB_FAR) == (int)s;
+        while (v > (int)s && p > 0) {
+            --p;
+            v = (int)((uint32_t)col[(long long)p * Np] & ~NB_FAR);
+        }
+        const bool ok = (v == (int)s);
         if (!ok) atomicOr(b.err, ERR_REV);
-        b.rev[(long long)k * Np + s] = (uint16_t)(ok ? lo - f0 : 0);
+        b.rev[(long long)k * Np + s] = (uint16_t)(ok ? p : 0);
     }
 }
 
