@@ -80,7 +80,7 @@ struct Bufs {
     // particle's own slot; rev = position of the pair in the lower partner's
     // owned part (Newton-3 pass)
     int *nbr, *ncnt, *nfirst;
-    uint16_t *rev;             // owned entry k of s -> position of s in the partner's list
+    uint16_t *rev;             // entry k of s below s -> position of s in the partner's owned part
     uint8_t *nbflag;           // per slot: bit 0 = has a rigid neighbour
     int capown;                // owned entries per particle in the pair buffer
     void *resA, *resB;         // pair results [capown][Npad]: R4 {f, t.x}, R2 {t.y, t.z}

@@ -258,36 +258,54 @@ __global__ void k_neighbors(Bufs b, int precision)
     b.ncnt[s] = cnt;
 }
 
-// For every owned entry of s (partner j > s), the position of s in the lower
-// part of j's list.  Lists are ascending, and consecutive partners of s are
-// mostly neighbours of each other, so the search walks from the previous
-// answer instead of bisecting.  The Newton-3 force pass writes the partner's
-// share of each pair result there.
+// For every entry of s's list below s (partner i < s), the position of s in
+// the owned (upper) part of i's list, by binary search (lists are ascending);
+// four searches run interleaved so their loads overlap.  The Newton-3 force
+// pass reads the pair result from there.
+__device__ __forceinline__ int nb_at(const Bufs &b, int i, int k)
+{
+    return (int)((uint32_t)__ldg(b.nbr + (long long)k * b.Npad + i) & ~NB_FAR);
+}
+
 __global__ void k_rev(Bufs b)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const long long Np = b.Npad;
-    const int first = b.nfirst[s], n = b.ncnt[s];
-    int p = 0;
-    for (int k = first; k < n; ++k) {
-        const int j = (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR);
-        const int lim = b.nfirst[j];
-        if (p >= lim) p = lim - 1;
-        if (p < 0) p = 0;
-        const int *col = b.nbr + j;
-        int v = lim > 0 ? (int)((uint32_t)col[(long long)p * Np] & ~NB_FAR) : -1;
-        while (v < (int)s && p + 1 < lim) {
-            ++p;
-            v = (int)((uint32_t)col[(long long)p * Np] & ~NB_FAR);
+    const int first = b.nfirst[s];
+    if (b.ncnt[s] - first > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+    constexpr int G = 4;
+    for (int k0 = 0; k0 < first; k0 += G) {
+        int part[G], lo[G], hi[G], f0[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int k = k0 + g;
+            part[g] = k < first ? (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR) : -1;
+            lo[g] = part[g] >= 0 ? b.nfirst[part[g]] : 0;
+            hi[g] = part[g] >= 0 ? b.ncnt[part[g]] : 0;
+            f0[g] = lo[g];
         }
-        while (v > (int)s && p > 0) {
-            --p;
-            v = (int)((uint32_t)col[(long long)p * Np] & ~NB_FAR);
+        bool active = true;
+        while (active) {
+            active = false;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (lo[g] < hi[g]) {
+                    const int mid = (lo[g] + hi[g]) >> 1;
+                    if (nb_at(b, part[g], mid) < (int)s) lo[g] = mid + 1;
+                    else hi[g] = mid;
+                    active = true;
+                }
+            }
         }
-        const bool ok = (v == (int)s);
-        if (!ok) atomicOr(b.err, ERR_REV);
-        b.rev[(long long)k * Np + s] = (uint16_t)(ok ? p : 0);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int k = k0 + g;
+            if (k >= first) break;
+            const bool ok = lo[g] < b.ncnt[part[g]] && nb_at(b, part[g], lo[g]) == (int)s;
+            if (!ok) atomicOr(b.err, ERR_REV);
+            b.rev[(long long)k * Np + s] = (uint16_t)(ok ? lo[g] - f0[g] : 0);
+        }
     }
 }
 
