@@ -204,6 +204,34 @@ sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
  * sdpd_step has not run yet).  Synchronous. */
 sdpd_status sdpd_graph_kernels(sdpd_ctx *ctx, long long *n_kernels);
 
+/* Largest particle and cell counts sdpd_density_noalloc accepts. */
+#define SDPD_NOALLOC_MAX_PARTICLES 131072
+#define SDPD_NOALLOC_MAX_CELLS 65536
+
+/* Number density d and pressure p ([n] doubles, device memory) of one
+ * particle set -- positions x ([n][3] doubles) and types ([n] int32), both in
+ * device memory -- under parameters *params, without allocating any device
+ * memory.  The paper has no counterpart: this exists for callers that cannot
+ * let a library allocate, such as applications whose own allocator owns the
+ * whole device and code that cannot afford the device-wide synchronisation
+ * cudaMalloc/cudaFree may cause.  The results equal those of
+ * sdpd_build_cells + sdpd_compute_density in FP64 with the filter off, up to
+ * summation order.
+ * Scratch: one file-scope __device__ array of about 2 MB (cell keys, slots,
+ * counts, starts, permutation) held by every GPU that loads the library until
+ * the process exits.  At most SDPD_NOALLOC_MAX_PARTICLES particles and
+ * SDPD_NOALLOC_MAX_CELLS cells of width >= r_c (periodic axes: floor(box/r_c)
+ * cells, >= 3; wall axes: the box plus 2 r_c on each side); larger inputs are
+ * rejected with SDPD_E_INVALID.  The first call on a device resolves the
+ * array's device address (with that device current) and should come before
+ * any stream capture.  Every call reuses the same array and leaves its
+ * contents behind: calls whose work overlaps on the GPU (different streams,
+ * different host threads) race and give wrong results; serialise them.
+ * Asynchronous on `stream`; no cudaMalloc, cudaFree or allocating library
+ * call is made. */
+sdpd_status sdpd_density_noalloc(const sdpd_params *params, long long n, const double *x,
+                                 const int *type, double *d_out, double *p_out, void *stream);
+
 /* Wait for all work of the context and report a pending kernel error. */
 sdpd_status sdpd_check(sdpd_ctx *ctx);
 

@@ -74,7 +74,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_compute_density", "sdpd_couple_drag", "sdpd_compute_forces", "sdpd_integrate",
            "sdpd_step", "sdpd_viscosity_probe", "sdpd_get_state", "sdpd_get_drag",
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
-           "sdpd_set_force_mode",
+           "sdpd_set_force_mode", "sdpd_density_noalloc",
            "sdpd_check",
            "sdpd_last_error"]
 
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True):
         "sdpd_diagnostics": (st, [vp, C.c_int, dp]),
         "sdpd_graph_kernels": (st, [vp, llp]),
         "sdpd_set_force_mode": (st, [vp, C.c_int]),
+        "sdpd_density_noalloc": (st, [C.POINTER(SdpdParams), C.c_longlong, vp, vp, vp, vp, vp]),
         "sdpd_check": (st, [vp]),
         "sdpd_last_error": (C.c_char_p, []),
     }
@@ -159,6 +160,20 @@ def _ptr(a):
     if isinstance(a, np.ndarray):
         return C.c_void_p(a.ctypes.data)
     return C.c_void_p(int(a.data_ptr()))
+
+
+NOALLOC_MAX_PARTICLES = 131072
+NOALLOC_MAX_CELLS = 65536
+
+
+def density_noalloc(params: dict, x, type_, d_out, p_out, stream=None):
+    """Number density and pressure of one particle set with no device
+    allocation (sdpd_density_noalloc).  x [n,3] float64, type_ [n] int32,
+    d_out / p_out [n] float64: device tensors (or device pointers)."""
+    prm = make_params(params)
+    n = int(x.shape[0])
+    _check(load().sdpd_density_noalloc(C.byref(prm), n, _ptr(x), _ptr(type_), _ptr(d_out),
+                                       _ptr(p_out), _stream(stream)))
 
 
 class Sim:

@@ -40,6 +40,8 @@ struct HostInst {
 
 }  // namespace
 
+void sdpd::set_last_error(const char *msg) { g_last_error = msg; }
+
 struct sdpd_ctx {
     int n_inst = 0, precision = 0, cap = 384, K = 16;
     long long N = 0, Npad = 0;

@@ -230,6 +230,9 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// message returned by sdpd_last_error() on this thread (defined in api.cu)
+void set_last_error(const char *msg);
+
 // ---------------------------------------------------------------- launchers
 // (defined in k_cells.cu, k_pairs.cu, k_update.cu; all enqueue on `st`)
 void launch_cell_keys(const Bufs &b, cudaStream_t st);
