@@ -200,6 +200,14 @@ sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
  * the current neighbour build and graph.  Synchronous. */
 sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
 
+/* Verlet skin as a fraction of h (default 0.03): neighbour lists hold the
+ * pairs within h (1 + skin) and are reused by later evaluations until some
+ * particle has moved skin h / 2 since the build (decided on the device each
+ * drift; the rebuild happens inside the step).  Every pass re-decides
+ * r_ij < h exactly, so results do not depend on the skin beyond summation
+ * order.  Invalidates the grid and the graph.  Synchronous. */
+sdpd_status sdpd_set_skin(sdpd_ctx *ctx, double skin);
+
 /* Number of kernel nodes in the captured one-step graph of sdpd_step (0 if
  * sdpd_step has not run yet).  Synchronous. */
 sdpd_status sdpd_graph_kernels(sdpd_ctx *ctx, long long *n_kernels);

@@ -53,6 +53,7 @@ struct sdpd_ctx {
     Inst *d_inst = nullptr;
     int any_filter = 0, any_artvis = 0;
     int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct
+    double skin = 0.03;                // Verlet skin as a fraction of h
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
     int sticky_err = 0;
     long long host_step = 0;
@@ -158,7 +159,8 @@ sdpd_status prepare(sdpd_ctx *c)
         const sdpd_params &p = H.P;
         Inst &I = c->inst[k];
         std::memset(&I, 0, sizeof(I));
-        const double cmin = std::max(p.r_c, 2.0 * H.Rmax);
+        const double rb = p.r_c * (1.0 + c->skin);
+        const double cmin = std::max(rb, 2.0 * H.Rmax + c->skin * p.r_c);
         for (int a = 0; a < 3; ++a) {
             I.origin[a] = p.origin[a];
             I.box[a] = p.box[a];
@@ -243,6 +245,10 @@ sdpd_status prepare(sdpd_ctx *c)
         I.coeff_cf = (float)p.coeff_c; I.coeff_df = (float)p.coeff_d;
         I.coeff_rf = (float)p.coeff_r; I.coeff_tf = (float)p.coeff_t;
         I.lever_fluidf = (float)I.lever_fluid;
+        I.rb = rb;
+        I.rb2 = rb * rb;
+        I.half_skin = 0.5 * c->skin * h;
+        I.rb2f = (float)(rb * rb * (1.0 + 1e-5));
         I.guard_lo = (float)(I.rc2 * (1.0 - 1e-5));
         I.guard_hi = (float)(I.rc2 * (1.0 + 1e-5));
         I.artvis_r2f_hi = (float)(I.artvis_rlim * I.artvis_rlim * (1.0 + 1e-5));
@@ -362,13 +368,10 @@ sdpd_status ensure_geometry(sdpd_ctx *c)
     return SDPD_OK;
 }
 
-void enqueue_build(sdpd_ctx *c, cudaStream_t st)
+void enqueue_build(sdpd_ctx *c, cudaStream_t st, const int *gate = nullptr)
 {
-    launch_cell_keys(c->b, st);
-    launch_scan_cells(c->b, st);
-    launch_scatter_rank(c->b, st);
-    launch_gather(c->b, c->precision, st);
-    launch_neighbors(c->b, c->precision, c->newton3, st);
+    c->b.use_cache = c->newton3;
+    launch_build(c->b, c->precision, c->newton3, gate, st);
 }
 
 }  // namespace
@@ -457,9 +460,25 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         IALLOC(ob, 2 * rs * (size_t)N);
         b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;
     }
+    IALLOC(b.xl64, N); IALLOC(b.dsp, N);
+    IALLOC(b.need_build, 1); IALLOC(b.fresh, 1);
+    IALLOC(b.list_epoch, 1); IALLOC(b.cache_epoch, 1); IALLOC(b.cache_step, 1);
+    {
+        const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
+        char *za = nullptr, *zb = nullptr;
+        IALLOC(za, 4 * rs * (size_t)c->cap * c->Npad);
+        IALLOC(zb, 2 * rs * (size_t)c->cap * c->Npad);
+        b.zA = za; b.zB = zb;
+    }
+    b.use_cache = 1;
     IALLOC(b.step, 1); IALLOC(b.err, 1); IALLOC(b.pair_count, 1);
     IALLOC(b.probe, 4096 * 2 + 64);
 #undef IALLOC
+    if (cudaMemset(b.need_build, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.fresh, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(b.list_epoch, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(b.cache_epoch, 0xFF, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(b.cache_step, 0xFF, sizeof(long long)) != cudaSuccess)
+        return cleanup(fail(SDPD_E_CUDA, "cudaMemset failed"));
     if (cudaMemset(b.err, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.step, 0, sizeof(long long)) != cudaSuccess ||
         cudaMemset(b.F, 0, sizeof(double) * (n3 ? n3 : 1)) != cudaSuccess ||
         cudaMemset(b.T, 0, sizeof(double) * (n3 ? n3 : 1)) != cudaSuccess)
@@ -617,7 +636,7 @@ sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
     (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->cells_valid) return fail(SDPD_E_STATE, "sdpd_build_cells must precede sdpd_compute_density");
-    launch_density(c->b, c->precision, c->any_filter, (cudaStream_t)stream);
+    launch_density(c->b, c->precision, c->any_filter, nullptr, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     c->density_valid = true;
     return SDPD_OK;
@@ -677,7 +696,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         c->density_valid = false;
     }
     if (!c->density_valid) {
-        launch_density(c->b, c->precision, c->any_filter, st);
+        launch_density(c->b, c->precision, c->any_filter, nullptr, st);
         c->density_valid = true;
     }
     if (!c->graph) {
@@ -686,12 +705,17 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         // the density exactly
         CUDA_TRY(cudaStreamSynchronize(st));
         CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        // Verlet skin: the list is rebuilt only when a drift has used up half
+        // the skin (device flag gating the build kernels); density is redone
+        // at velver 1 only after such a build, at velver 2 always
         cudaStream_t cs = c->cap_stream;
+        enqueue_build(c, cs, c->b.need_build);
+        launch_density(c->b, c->precision, c->any_filter, c->b.fresh, cs);
         launch_drag(c->b, cs);
         launch_forces(c->b, c->precision, 1, c->newton3, cs);
         launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
-        enqueue_build(c, cs);
-        launch_density(c->b, c->precision, c->any_filter, cs);
+        enqueue_build(c, cs, c->b.need_build);
+        launch_density(c->b, c->precision, c->any_filter, nullptr, cs);
         launch_drag(c->b, cs);
         launch_forces(c->b, c->precision, 2, c->newton3, cs);
         launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);
@@ -716,6 +740,20 @@ sdpd_status sdpd_set_force_mode(sdpd_ctx *c, int newton3)
     CUDA_TRY(cudaDeviceSynchronize());
     if (newton3 != c->newton3) {
         c->newton3 = newton3;
+        drop_graph(c);
+        c->cells_valid = c->density_valid = c->drag_valid = false;
+    }
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_set_skin(sdpd_ctx *c, double skin)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (!(skin >= 0.0 && skin <= 0.5)) return fail(SDPD_E_INVALID, "skin must be in [0, 0.5]");
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (skin != c->skin) {
+        c->skin = skin;
+        c->geometry_ready = false;
         drop_graph(c);
         c->cells_valid = c->density_valid = c->drag_valid = false;
     }
@@ -832,7 +870,17 @@ sdpd_status sdpd_get_pairs(sdpd_ctx *c, int inst, long long cap, int *ij, long l
     int kmax = 0;
     for (long long s = 0; s < N; ++s) kmax = std::max(kmax, cnt[s]);
     std::vector<int> nb((size_t)kmax * c->Npad);
-    if (kmax) CUDA_TRY(cudaMemcpy(nb.data(), c->b.nbr, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> fl((size_t)kmax * c->Npad);
+    if (kmax) {
+        // entries of the (skin) list within h at the current positions
+        uint8_t *dfl = nullptr;
+        CUDA_TRY(cudaMalloc(&dfl, (size_t)c->cap * c->Npad));
+        launch_mark_pairs(c->b, dfl, 0);
+        cudaError_t e1 = cudaMemcpy(fl.data(), dfl, fl.size(), cudaMemcpyDeviceToHost);
+        cudaFree(dfl);
+        if (e1 != cudaSuccess) return fail(SDPD_E_CUDA, "cudaMemcpy pair flags");
+        CUDA_TRY(cudaMemcpy(nb.data(), c->b.nbr, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost));
+    }
     const long long o = c->hi[inst].begin;
     long long k = 0;
     for (long long s = 0; s < N; ++s) {
@@ -840,7 +888,7 @@ sdpd_status sdpd_get_pairs(sdpd_ctx *c, int inst, long long cap, int *ij, long l
         if (pinst[gi] != inst) continue;
         for (int q = 0; q < cnt[s]; ++q) {
             const uint32_t e = (uint32_t)nb[(size_t)q * c->Npad + s];
-            if (e & NB_FAR) continue;
+            if ((e & NB_FAR) || !fl[(size_t)q * c->Npad + s]) continue;
             const int gj = perm[e];
             if (gj <= gi) continue;
             if (k < cap && ij) {

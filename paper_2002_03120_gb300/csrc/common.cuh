@@ -53,6 +53,10 @@ struct Inst {
     float coeff_cf, coeff_df, coeff_rf, coeff_tf, W0f, lever_fluidf;
     float guard_lo, guard_hi;   // r^2 band re-decided exactly in double
     float artvis_r2f_hi;        // collision pass: float prefilter bound
+    // Verlet skin: lists hold pairs within rb = h (1 + skin); they stay valid
+    // until a particle has moved skin h / 2 since the build
+    double rb, rb2, half_skin;
+    float rb2f;
 };
 
 // Device buffers of a context (all device pointers).
@@ -93,6 +97,16 @@ struct Bufs {
     double *h_del, *hn_del;
     // artificial viscosity scratch
     double *dv;
+    // list reuse: exact cell-relative coordinates and displacement since the
+    // last build (slot order); build gate and epochs; cached random normals
+    double4_32a *xl64, *dsp;
+    int *need_build;           // set by the drift when a particle moved half the skin
+    unsigned *list_epoch;      // incremented by every build
+    unsigned *cache_epoch;     // list epoch of the cached normals
+    long long *cache_step;     // step of the cached normals
+    void *zA, *zB;             // normals [capown][Npad]: R4 {z0..z3}, R2 {z4, z5}
+    int use_cache;
+    int *fresh;                // a build happened since the last density
     // counters
     long long *step;
     int *err;
@@ -230,19 +244,43 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// The oracle's distance: r = x_i - x_j with the minimum image on periodic
+// axes, r^2 = (x*x + y*y) + z*z, evaluated without fused multiply-adds.
+__device__ __forceinline__ double exact_r2(const double *xi, const double *xj, const Inst &I)
+{
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double t = __dsub_rn(xi[a], xj[a]);
+        if (I.periodic[a]) {
+            const double hL = 0.5 * I.box[a];
+            if (t > hL) t = __dsub_rn(t, I.box[a]);
+            else if (t < -hL) t = __dadd_rn(t, I.box[a]);
+        }
+        d[a] = t;
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+// r_ij < h decided exactly from the FP64 master positions (gids gi, gj).
+__device__ __forceinline__ bool exact_within(const Bufs &b, const Inst &I, int gi, int gj)
+{
+    const double xi[3] = { b.x[3 * gi], b.x[3 * gi + 1], b.x[3 * gi + 2] };
+    const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+    return exact_r2(xi, xj, I) < I.rc2;
+}
+
 // message returned by sdpd_last_error() on this thread (defined in api.cu)
 void set_last_error(const char *msg);
 
 // ---------------------------------------------------------------- launchers
 // (defined in k_cells.cu, k_pairs.cu, k_update.cu; all enqueue on `st`)
-void launch_cell_keys(const Bufs &b, cudaStream_t st);
-void launch_scan_cells(const Bufs &b, cudaStream_t st);
-void launch_scatter_rank(const Bufs &b, cudaStream_t st);
-void launch_gather(const Bufs &b, int precision, cudaStream_t st);
-void launch_neighbors(const Bufs &b, int precision, int need_rev, cudaStream_t st);
-void launch_density(const Bufs &b, int precision, int any_filter, cudaStream_t st);
+// gate: nullptr = always build; else build only when *gate != 0
+void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, cudaStream_t st);
+void launch_density(const Bufs &b, int precision, int any_filter, const int *gate, cudaStream_t st);
 void launch_drag(const Bufs &b, cudaStream_t st);
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st);
+void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st);
 void launch_integrate(const Bufs &b, int precision, int velver, int any_artvis, cudaStream_t st);
 void launch_step_done(const Bufs &b, cudaStream_t st);
 void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long n);

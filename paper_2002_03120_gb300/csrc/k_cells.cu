@@ -6,12 +6,21 @@
 //   K2 exclusive scan of the counts -> cell starts
 //   K3 scatter into cell ranges, K4 rank by gid inside each cell (deterministic
 //      order, so every later sum is reproducible bit for bit)
-//   K5 gather of the cell-sorted mirrors (float4 / double4_32a records)
-//   K6 per particle, the list of neighbours j != i with r_ij < h from the 27
-//      surrounding cells (exact FP64 decision, FP32 prefilter in split mode)
+//   K5 gather of the cell-sorted mirrors (float4 / double4 records)
+//   K6 per particle, the ascending list of neighbours j != i within the build
+//      radius rb = h (1 + skin) from the surrounding cells
+//   K7 reverse index of the Newton-3 force pass
+// The list is a superset of the pairs within h; every consumer re-decides
+// r_ij < h exactly, so the evaluated pair set equals the paper's.  The list
+// stays valid while no particle has moved more than skin h / 2 since the
+// build; the drift raises `need_build` when one has, and every kernel here
+// is gated on that flag inside the captured step.
 #include "common.cuh"
 
 namespace sdpd {
+
+#define GATE                                                                                    \
+    if (gate && *gate == 0) return;
 
 __device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc, bool &out)
 {
@@ -20,8 +29,16 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, in
     return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
 }
 
-__global__ void k_cell_keys(Bufs b)
+__global__ void k_cell_clear(Bufs b, const int *gate)
 {
+    GATE;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < b.ncell_total) b.ccount[c] = 0;
+}
+
+__global__ void k_cell_keys(Bufs b, const int *gate)
+{
+    GATE;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= b.N) return;
     const Inst &I = b.inst[b.pinst[g]];
@@ -70,48 +87,55 @@ __device__ int block_excl_scan(int v, int *total)
     return off + inc - v;
 }
 
-__global__ void k_scan_local(const int *cnt, int *start, int *partials, int n)
+__global__ void k_scan_local(Bufs b, const int *gate)
 {
+    GATE;
+    const int n = b.ncell_total;
     const int i = blockIdx.x * 1024 + threadIdx.x;
-    const int v = i < n ? cnt[i] : 0;
+    const int v = i < n ? b.ccount[i] : 0;
     int tot;
     const int e = block_excl_scan(v, &tot);
-    if (i < n) start[i] = e;
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+    if (i < n) b.cstart[i] = e;
+    if (threadIdx.x == 0) b.scan_partials[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_partials(int *partials, int nblk)
+__global__ void k_scan_partials(Bufs b, int nblk, const int *gate)
 {
+    GATE;
     // one block of 1024 threads, sequential over chunks
     int carry = 0;
     for (int base = 0; base < nblk; base += 1024) {
         const int i = base + threadIdx.x;
-        const int v = i < nblk ? partials[i] : 0;
+        const int v = i < nblk ? b.scan_partials[i] : 0;
         int tot;
         const int e = block_excl_scan(v, &tot);
-        if (i < nblk) partials[i] = carry + e;
+        if (i < nblk) b.scan_partials[i] = carry + e;
         carry += tot;
         __syncthreads();
     }
 }
 
-__global__ void k_scan_add(int *start, const int *partials, int n, long long N)
+__global__ void k_scan_add(Bufs b, const int *gate)
 {
+    GATE;
+    const int n = b.ncell_total;
     const int i = blockIdx.x * 1024 + threadIdx.x;
-    if (i < n) start[i] += partials[blockIdx.x];
-    if (i == 0) start[n] = (int)N;
+    if (i < n) b.cstart[i] += b.scan_partials[blockIdx.x];
+    if (i == 0) b.cstart[n] = (int)b.N;
 }
 
-__global__ void k_scatter(Bufs b)
+__global__ void k_scatter(Bufs b, const int *gate)
 {
+    GATE;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= b.N) return;
     b.tmp_perm[b.cstart[b.key[g]] + b.slot_in_cell[g]] = (int)g;
 }
 
 // Rank of each particle among its cell's members by gid (stable, unique).
-__global__ void k_rank(Bufs b)
+__global__ void k_rank(Bufs b, const int *gate)
 {
+    GATE;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= b.N) return;
     const int g = b.tmp_perm[t];
@@ -123,9 +147,11 @@ __global__ void k_rank(Bufs b)
     b.slot_of[g] = s0 + r;
 }
 
-// Cell-sorted mirrors for the pair kernels.
-__global__ void k_gather(Bufs b, int precision)
+// Cell-sorted mirrors for the pair kernels; resets the displacement since
+// the build.
+__global__ void k_gather(Bufs b, int precision, const int *gate)
 {
+    GATE;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const int g = b.perm[s];
@@ -136,8 +162,8 @@ __global__ void k_gather(Bufs b, int precision)
     const double x0 = b.x[3 * g], x1 = b.x[3 * g + 1], x2 = b.x[3 * g + 2];
     const uint32_t lg = (uint32_t)(g - I.p_begin);
     {
-        // cell-relative float coordinates (both precisions: the neighbour
-        // search and the collision pass prefilter on them)
+        // cell-relative coordinates (both precisions: the neighbour search
+        // and the split-precision pair kernels work on them)
         int c[3];
         double xl[3];
         const double xs[3] = { x0, x1, x2 };
@@ -149,6 +175,8 @@ __global__ void k_gather(Bufs b, int precision)
         }
         b.A32[s] = make_float4((float)xl[0], (float)xl[1], (float)xl[2],
                                __uint_as_float(pack_cell(t, c[0], c[1], c[2])));
+        b.xl64[s] = make_double4_32a(xl[0], xl[1], xl[2], 0.0);
+        b.dsp[s] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     }
     if (precision == SDPD_PREC_SPLIT) {
         b.B32[s] = make_float4((float)b.v[3 * g], (float)b.v[3 * g + 1], (float)b.v[3 * g + 2],
@@ -164,51 +192,31 @@ __global__ void k_gather(Bufs b, int precision)
     }
 }
 
-// The oracle's distance: r = x_i - x_j with the minimum image on periodic
-// axes, r^2 = (x*x + y*y) + z*z, evaluated without fused multiply-adds.
-__device__ __forceinline__ double exact_r2(const double *xi, const double *xj, const Inst &I)
+// Neighbour list of particle (slot) s: candidates from the cells around s's
+// cell (cells are at least max(rb, largest sphere diameter + skin) wide,
+// periodic axes at least 3 cells), visited in ascending key order so the list
+// comes out ascending in slot.  A pair is listed when r < rb (float test: the
+// list only has to be a superset of the pairs within h), or when both are
+// rigid and r < R_i + R_j + skin h (contact range; flagged NB_FAR).
+__global__ void k_neighbors(Bufs b, const int *gate)
 {
-    double d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double t = __dsub_rn(xi[a], xj[a]);
-        if (I.periodic[a]) {
-            const double hL = 0.5 * I.box[a];
-            if (t > hL) t = __dsub_rn(t, I.box[a]);
-            else if (t < -hL) t = __dadd_rn(t, I.box[a]);
-        }
-        d[a] = t;
-    }
-    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-}
-
-// Neighbour list of particle (slot) s.  Candidates come from the 27 cells
-// around s's cell (cells are at least max(h, largest sphere diameter) wide,
-// periodic axes at least 3 cells).  A pair is listed when r < h, or when both
-// are rigid and r < R_i + R_j (contact only, flagged NB_FAR).
-__global__ void k_neighbors(Bufs b, int precision)
-{
+    GATE;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const int gi = b.perm[s];
     const Inst &I = b.inst[b.pinst[gi]];
     const int ti = b.stype[s];
-    const double xi[3] = { b.x[3 * gi], b.x[3 * gi + 1], b.x[3 * gi + 2] };
-    const double Ri = (ti == T_RIGID) ? b.R[gi] : 0.0;
-    int ci[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        bool o;
-        ci[a] = cell_coord(xi[a], I.lo[a], I.inv_cs[a], I.nc[a], o);
-    }
+    const float Ri = (ti == T_RIGID) ? (float)b.R[gi] : 0.f;
     const float4 Ai = b.A32[s];
-    const float glo = I.guard_lo, ghi = I.guard_hi;
-    const int key_i = I.cell_base + b.cell_rank[I.cell_base + (ci[2] * I.nc[1] + ci[1]) * I.nc[0] + ci[0]];
+    const uint32_t bits = __float_as_uint(Ai.w);
+    const int key_i =
+        I.cell_base + b.cell_rank[I.cell_base + (unpack_cz(bits) * I.nc[1] + unpack_cy(bits)) * I.nc[0] + unpack_cx(bits)];
     const int *adj = b.cell_adj + (long long)key_i * 27;
+    const float rbf = I.rb2f;
+    const float skinr = (float)(2.0 * I.half_skin);
     int cnt = 0, nlow = 0;
     bool rig = false;
     const long long Np = b.Npad;
-    // neighbour cells in ascending key order: the list comes out sorted by slot
     for (int q = 0; q < 27; ++q) {
         const int code = adj[q];
         if (code < 0) break;
@@ -221,27 +229,16 @@ __global__ void k_neighbors(Bufs b, int precision)
             if (j == s) continue;
             const float4 Aj = b.A32[j];
             const int tj = unpack_type(__float_as_uint(Aj.w));
-            const bool both_rigid = (ti == T_RIGID) && (tj == T_RIGID);
             const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy, dz = (Ai.z - Aj.z) - sz;
             const float r2f = dx * dx + dy * dy + dz * dz;
-            // 1 in, 0 out, -1: inside the guard band, decide exactly
-            int decide = both_rigid ? -1 : ((r2f < glo) ? 1 : ((r2f > ghi) ? 0 : -1));
             uint32_t entry = (uint32_t)j;
-            if (decide < 0) {
-                const int gj = b.perm[j];
-                const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-                const double r2 = exact_r2(xi, xj, I);
-                if (r2 < I.rc2) {
-                    decide = 1;
-                } else if (both_rigid) {
-                    const double ds = (Ri + b.R[gj]) * (1.0 + 1e-9);
-                    decide = (r2 < ds * ds) ? 1 : 0;
-                    entry |= NB_FAR;
-                } else {
-                    decide = 0;
-                }
+            bool in = r2f < rbf;
+            if (!in && ti == T_RIGID && tj == T_RIGID) {
+                const float lim = (Ri + (float)b.R[b.perm[j]] + skinr) * 1.0001f;
+                in = r2f < lim * lim;
+                entry |= NB_FAR;
             }
-            if (decide == 1) {
+            if (in) {
                 if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
                 ++cnt;
                 nlow += (j < s);
@@ -249,13 +246,13 @@ __global__ void k_neighbors(Bufs b, int precision)
             }
         }
     }
-    b.nfirst[s] = nlow < b.cap ? nlow : b.cap;
-    b.nbflag[s] = rig ? 1 : 0;
     if (cnt > b.cap) {
         atomicOr(b.err, ERR_NBR_CAP);
         cnt = b.cap;
     }
     b.ncnt[s] = cnt;
+    b.nfirst[s] = nlow < b.cap ? nlow : b.cap;
+    b.nbflag[s] = rig ? 1 : 0;
 }
 
 // For every entry of s's list below s (partner i < s), the position of s in
@@ -267,8 +264,9 @@ __device__ __forceinline__ int nb_at(const Bufs &b, int i, int k)
     return (int)((uint32_t)__ldg(b.nbr + (long long)k * b.Npad + i) & ~NB_FAR);
 }
 
-__global__ void k_rev(Bufs b)
+__global__ void k_rev(Bufs b, const int *gate)
 {
+    GATE;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const long long Np = b.Npad;
@@ -309,41 +307,35 @@ __global__ void k_rev(Bufs b)
     }
 }
 
+// Closes the build: a new list epoch, the gate shut until the skin is used up.
+__global__ void k_build_done(Bufs b, const int *gate)
+{
+    GATE;
+    *b.list_epoch += 1u;
+    *b.need_build = 0;
+    *b.fresh = 1;
+}
+
 // ---------------------------------------------------------------- launchers
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-void launch_cell_keys(const Bufs &b, cudaStream_t st)
+void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, cudaStream_t st)
 {
-    cudaMemsetAsync(b.ccount, 0, sizeof(int) * (size_t)b.ncell_total, st);
-    if (b.N) k_cell_keys<<<nblk(b.N, 256), 256, 0, st>>>(b);
-}
-
-void launch_scan_cells(const Bufs &b, cudaStream_t st)
-{
-    const int n = b.ncell_total;
-    const int nb = (n + 1023) / 1024;
-    k_scan_local<<<nb, 1024, 0, st>>>(b.ccount, b.cstart, b.scan_partials, n);
-    k_scan_partials<<<1, 1024, 0, st>>>(b.scan_partials, nb);
-    k_scan_add<<<nb, 1024, 0, st>>>(b.cstart, b.scan_partials, n, b.N);
-}
-
-void launch_scatter_rank(const Bufs &b, cudaStream_t st)
-{
-    if (!b.N) return;
-    k_scatter<<<nblk(b.N, 256), 256, 0, st>>>(b);
-    k_rank<<<nblk(b.N, 256), 256, 0, st>>>(b);
-}
-
-void launch_gather(const Bufs &b, int precision, cudaStream_t st)
-{
-    if (b.N) k_gather<<<nblk(b.N, 256), 256, 0, st>>>(b, precision);
-}
-
-void launch_neighbors(const Bufs &b, int precision, int need_rev, cudaStream_t st)
-{
-    if (!b.N) return;
-    k_neighbors<<<nblk(b.N, 128), 128, 0, st>>>(b, precision);
-    if (need_rev) k_rev<<<nblk(b.N, 128), 128, 0, st>>>(b);
+    const int nc = b.ncell_total;
+    const int nbk = (nc + 1023) / 1024;
+    k_cell_clear<<<nblk(nc, 256), 256, 0, st>>>(b, gate);
+    if (b.N) k_cell_keys<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
+    k_scan_local<<<nbk, 1024, 0, st>>>(b, gate);
+    k_scan_partials<<<1, 1024, 0, st>>>(b, nbk, gate);
+    k_scan_add<<<nbk, 1024, 0, st>>>(b, gate);
+    if (b.N) {
+        k_scatter<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
+        k_rank<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
+        k_gather<<<nblk(b.N, 256), 256, 0, st>>>(b, precision, gate);
+        k_neighbors<<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
+        if (need_rev) k_rev<<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
+    }
+    k_build_done<<<1, 1, 0, st>>>(b, gate);
 }
 
 }  // namespace sdpd

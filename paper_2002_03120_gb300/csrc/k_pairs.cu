@@ -4,16 +4,21 @@
 //                  prtcpres; kernel normalisation; negative-pressure clamp)
 //   k_filter       smoothe_particle_pres (Shepard-weighted pressure)
 //   k_drag         compute_fpi_action (Eqs. fvfdef, beta, F_fpi_DG)
-//   k_force_fluid  compute_fluid on fluid particles + compute_fpi_reaction
+//   k_force_half + k_force_gather (Newton-3) or k_force_fluid (direct):
+//                  compute_fluid on fluid particles + compute_fpi_reaction
 //                  (Eqs. FijC, FijD, FijR, FijT, F_fpi_DG_reac) + torque
 //   k_force_rigid  compute_fluid on rigid particles (Eq. F_fpi_PG) +
 //                  compute_rigid (Eqs. dem_fnij .. slideref, lubri), FP64
 //
-// Ownership: the thread of particle i sums every pair (i, j) of its list and
-// writes only particle i -- no atomics, no write races; each unordered pair is
-// evaluated by both owners with expressions symmetric in (i, j), so the two
-// results are exact negatives.  The random matrix of a pair is regenerated by
-// both owners from the counter (min gid, max gid, step).
+// Neighbour lists hold every pair within the build radius h (1 + skin); each
+// pass decides r_ij < h exactly before using a pair (float test outside a
+// +-1e-5 guard band, the oracle's double expression inside it, or the double
+// expression directly in FP64 mode), so the pairs evaluated are exactly the
+// paper's.  No atomics on forces: a thread writes only its own particle, and
+// the Newton-3 pass hands each pair result to the partner through a buffer;
+// every sum has a fixed order.  The random matrix of a pair is regenerated
+// from the counter (min gid, max gid, step) or, in the second evaluation of a
+// step, read back from the first one's cache (same counter, same bits).
 #include "common.cuh"
 
 namespace sdpd {
@@ -21,6 +26,9 @@ namespace sdpd {
 template <class R> struct Vec;
 template <> struct Vec<float> { using T4 = float4; };
 template <> struct Vec<double> { using T4 = double4_32a; };
+template <class R> struct Vec2;
+template <> struct Vec2<float> { using T2 = float2; };
+template <> struct Vec2<double> { using T2 = double2; };
 
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
@@ -40,41 +48,6 @@ template <> struct Mir<double> {
     __device__ __forceinline__ static double4_32a *D(const Bufs &b) { return b.D64; }
 };
 
-// r_ij = r_i - r_j.  Split precision: positions relative to the own cell,
-// r = (xl_i - xl_j) + (c_i - c_j) * cell, with the cell difference taken to
-// the nearest periodic image (grids have >= 3 cells on periodic axes).  FP64:
-// absolute positions and the minimum image, as in the oracle.
-__device__ __forceinline__ void disp(const float4 &Ai, const float4 &Aj, const Inst &I, float &rx,
-                                     float &ry, float &rz)
-{
-    const uint32_t bi = __float_as_uint(Ai.w), bj = __float_as_uint(Aj.w);
-    int d0 = unpack_cx(bi) - unpack_cx(bj), d1 = unpack_cy(bi) - unpack_cy(bj),
-        d2 = unpack_cz(bi) - unpack_cz(bj);
-    if (I.periodic[0]) { if (d0 > 1) d0 -= I.nc[0]; else if (d0 < -1) d0 += I.nc[0]; }
-    if (I.periodic[1]) { if (d1 > 1) d1 -= I.nc[1]; else if (d1 < -1) d1 += I.nc[1]; }
-    if (I.periodic[2]) { if (d2 > 1) d2 -= I.nc[2]; else if (d2 < -1) d2 += I.nc[2]; }
-    rx = (Ai.x - Aj.x) + (float)d0 * I.csf[0];
-    ry = (Ai.y - Aj.y) + (float)d1 * I.csf[1];
-    rz = (Ai.z - Aj.z) + (float)d2 * I.csf[2];
-}
-
-__device__ __forceinline__ double min_img(double d, const Inst &I, int a)
-{
-    if (!I.periodic[a]) return d;
-    const double hL = 0.5 * I.box[a];
-    if (d > hL) return d - I.box[a];
-    if (d < -hL) return d + I.box[a];
-    return d;
-}
-
-__device__ __forceinline__ void disp(const double4_32a &Ai, const double4_32a &Aj, const Inst &I, double &rx,
-                                     double &ry, double &rz)
-{
-    rx = min_img(Ai.x - Aj.x, I, 0);
-    ry = min_img(Ai.y - Aj.y, I, 1);
-    rz = min_img(Ai.z - Aj.z, I, 2);
-}
-
 __device__ __forceinline__ int mir_type(const float4 &A) { return unpack_type(__float_as_uint(A.w)); }
 __device__ __forceinline__ int mir_type(const double4_32a &A) { return (int)A.w; }
 __device__ __forceinline__ uint32_t mir_gid(const float4 &D) { return __float_as_uint(D.w); }
@@ -82,7 +55,6 @@ __device__ __forceinline__ uint32_t mir_gid(const double4_32a &D) { return (uint
 
 template <class R> struct K;  // kernel constants in precision R
 template <> struct K<float> {
-    __device__ __forceinline__ static float rc(const Inst &I) { return I.rcf; }
     __device__ __forceinline__ static float inv_rc(const Inst &I) { return I.inv_rcf; }
     __device__ __forceinline__ static float Wc(const Inst &I) { return I.Wcf; }
     __device__ __forceinline__ static float Fc(const Inst &I) { return I.Fcf; }
@@ -99,7 +71,6 @@ template <> struct K<float> {
     __device__ __forceinline__ static float lever(const Inst &I) { return I.lever_fluidf; }
 };
 template <> struct K<double> {
-    __device__ __forceinline__ static double rc(const Inst &I) { return I.rc; }
     __device__ __forceinline__ static double inv_rc(const Inst &I) { return 1.0 / I.rc; }
     __device__ __forceinline__ static double Wc(const Inst &I) { return I.Wc; }
     __device__ __forceinline__ static double Fc(const Inst &I) { return I.Fc; }
@@ -116,6 +87,32 @@ template <> struct K<double> {
     __device__ __forceinline__ static double lever(const Inst &I) { return I.lever_fluid; }
 };
 
+// Displacement r_ij = r_i - r_j from the mirrors and the exact decision
+// r_ij < h (gi: gid of i; j: slot of the partner, used only in the band).
+template <class R> struct Rel;
+template <> struct Rel<float> {
+    __device__ __forceinline__ static bool get(const Bufs &b, const Inst &I, const Geo<float> &geo,
+                                               const float4 &Ai, const float4 &Aj, int gi, int j,
+                                               float &rx, float &ry, float &rz, float &r2)
+    {
+        geo.disp(Ai, Aj, rx, ry, rz);
+        r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < I.guard_lo) return true;
+        if (r2 > I.guard_hi) return false;
+        return exact_within(b, I, gi, b.perm[j]);
+    }
+};
+template <> struct Rel<double> {
+    __device__ __forceinline__ static bool get(const Bufs &, const Inst &I, const Geo<double> &geo,
+                                               const double4_32a &Ai, const double4_32a &Aj, int, int,
+                                               double &rx, double &ry, double &rz, double &r2)
+    {
+        geo.disp(Ai, Aj, rx, ry, rz);
+        r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+        return r2 < I.rc2;
+    }
+};
+
 // Neumaier-compensated running sum (split precision density and filter).
 struct KSum {
     float s, c;
@@ -126,6 +123,19 @@ struct KSum {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <class R> struct Acc;
+template <> struct Acc<float> {
+    KSum k;
+    __device__ __forceinline__ explicit Acc(double v0) : k{ (float)v0, 0.f } {}
+    __device__ __forceinline__ void add(float v) { k.add(v); }
+    __device__ __forceinline__ double value() const { return k.value(); }
+};
+template <> struct Acc<double> {
+    double s;
+    __device__ __forceinline__ explicit Acc(double v0) : s(v0) {}
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
 };
 
 // Per-particle quantities the force pass reads: p/d^2, 1/d, 1/sqrt(d).
@@ -141,9 +151,11 @@ __device__ __forceinline__ void finalize_slot(const Bufs &b, long long s, double
 }
 
 // ------------------------------------------------------------------ density
+// gate: nullptr = always; else only when *gate != 0 (a build just happened)
 template <class R>
-__global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter)
+__global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter, const int *gate)
 {
+    if (gate && *gate == 0) return;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const int gi = b.perm[s];
@@ -155,40 +167,21 @@ __global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter)
     } else {
         const auto *A = Mir<R>::A(b);
         const auto Ai = A[s];
+        const Geo<R> geo(I);
         const int n = b.ncnt[s];
         const long long Np = b.Npad;
         const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
-        double sum;
-        if (sizeof(R) == 4) {
-            KSum acc{ (float)K<R>::W0(I), 0.f };
-            for (int k = 0; k < n; ++k) {
-                const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
-                if (e & NB_FAR) continue;
-                const auto Aj = A[e];
-                R rx, ry, rz;
-                disp(Ai, Aj, I, rx, ry, rz);
-                const R r2 = rx * rx + ry * ry + rz * rz;
-                const R q = sqrt(r2) * irc;
-                const R om = q < R(1) ? R(1) - q : R(0);
-                acc.add((float)(Wc * (R(1) + R(3) * q) * om * om * om));
-            }
-            sum = acc.value();
-        } else {
-            double acc = I.W0;
-            for (int k = 0; k < n; ++k) {
-                const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
-                if (e & NB_FAR) continue;
-                const auto Aj = A[e];
-                R rx, ry, rz;
-                disp(Ai, Aj, I, rx, ry, rz);
-                const R r2 = rx * rx + ry * ry + rz * rz;
-                const R q = sqrt(r2) * irc;
-                const R om = q < R(1) ? R(1) - q : R(0);
-                acc += (double)(Wc * (R(1) + R(3) * q) * om * om * om);
-            }
-            sum = acc;
+        Acc<R> acc(I.W0);
+        for (int k = 0; k < n; ++k) {
+            const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
+            if (e & NB_FAR) continue;
+            R rx, ry, rz, r2;
+            if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
+            const R q = sqrt(r2) * irc;
+            const R om = q < R(1) ? R(1) - q : R(0);
+            acc.add(Wc * (R(1) + R(3) * q) * om * om * om);
         }
-        d = I.Cn * sum;
+        d = I.Cn * acc.value();
     }
     const double rho = I.mf * d;
     double p = I.p0 * pow(rho / I.rho0, I.alpha) - I.beta_p;
@@ -203,8 +196,9 @@ __global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter)
 
 // ------------------------------------------------------------ pressure filter
 template <class R>
-__global__ void __launch_bounds__(128) k_filter(Bufs b)
+__global__ void __launch_bounds__(128) k_filter(Bufs b, const int *gate)
 {
+    if (gate && *gate == 0) return;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const int gi = b.perm[s];
@@ -214,41 +208,23 @@ __global__ void __launch_bounds__(128) k_filter(Bufs b)
     if (I.filter && b.stype[s] != T_OUTER) {
         const auto *A = Mir<R>::A(b);
         const auto Ai = A[s];
+        const Geo<R> geo(I);
         const int n = b.ncnt[s];
         const long long Np = b.Npad;
         const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
-        if (sizeof(R) == 4) {
-            const float w0 = (float)I.W0;
-            KSum num{ (float)pi * w0, 0.f }, den{ w0, 0.f };
-            for (int k = 0; k < n; ++k) {
-                const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
-                if (e & NB_FAR) continue;
-                const auto Aj = A[e];
-                R rx, ry, rz;
-                disp(Ai, Aj, I, rx, ry, rz);
-                const R q = sqrt(rx * rx + ry * ry + rz * rz) * irc;
-                const R om = q < R(1) ? R(1) - q : R(0);
-                const float W = (float)(Wc * (R(1) + R(3) * q) * om * om * om);
-                num.add((float)b.sp[e] * W);
-                den.add(W);
-            }
-            pf = num.value() / den.value();
-        } else {
-            double num = pi * I.W0, den = I.W0;
-            for (int k = 0; k < n; ++k) {
-                const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
-                if (e & NB_FAR) continue;
-                const auto Aj = A[e];
-                R rx, ry, rz;
-                disp(Ai, Aj, I, rx, ry, rz);
-                const R q = sqrt(rx * rx + ry * ry + rz * rz) * irc;
-                const R om = q < R(1) ? R(1) - q : R(0);
-                const double W = (double)(Wc * (R(1) + R(3) * q) * om * om * om);
-                num += b.sp[e] * W;
-                den += W;
-            }
-            pf = num / den;
+        Acc<R> num(pi * I.W0), den(I.W0);
+        for (int k = 0; k < n; ++k) {
+            const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
+            if (e & NB_FAR) continue;
+            R rx, ry, rz, r2;
+            if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
+            const R q = sqrt(r2) * irc;
+            const R om = q < R(1) ? R(1) - q : R(0);
+            const R W = Wc * (R(1) + R(3) * q) * om * om * om;
+            num.add((R)b.sp[e] * W);
+            den.add(W);
         }
+        pf = num.value() / den.value();
     }
     b.sp2[s] = pf;
     finalize_slot<R>(b, s, b.sd[s], pf);
@@ -262,11 +238,20 @@ __device__ __forceinline__ double W_d(double r, const Inst &I)
     return I.Wc * (1.0 + 3.0 * q) * om * om * om;
 }
 
+// r = x_i - x_j with the minimum image; returns the oracle's r^2 (no FMA).
 __device__ __forceinline__ double exact_disp(const double *xi, const double *xj, const Inst &I, double r[3])
 {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) r[a] = min_img(xi[a] - xj[a], I, a);
-    return (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+    for (int a = 0; a < 3; ++a) {
+        double t = __dsub_rn(xi[a], xj[a]);
+        if (I.periodic[a]) {
+            const double hL = 0.5 * I.box[a];
+            if (t > hL) t = __dsub_rn(t, I.box[a]);
+            else if (t < -hL) t = __dadd_rn(t, I.box[a]);
+        }
+        r[a] = t;
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
 }
 
 // Per rigid particle s (one warp each, lanes striding over its neighbour
@@ -291,13 +276,16 @@ __global__ void k_drag(Bufs b)
         if (e & NB_FAR) continue;
         const int gj = b.perm[e];
         const int tj = b.type[gj];
+        if (tj != T_RIGID && tj != T_FLUID) continue;
+        const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+        double rv[3];
+        const double r2 = exact_disp(xi, xj, I, rv);
+        if (!(r2 < I.rc2)) continue;
         if (tj == T_RIGID) {
             const double Rj = b.R[gj];
             Vsum += 4.0 / 3.0 * PI * Rj * Rj * Rj;
-        } else if (tj == T_FLUID) {
-            const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-            double rv[3];
-            const double W = W_d(sqrt(exact_disp(xi, xj, I, rv)), I);
+        } else {
+            const double W = W_d(sqrt(r2), I);
             S += W;
             U0 += W * b.v[3 * gj];
             U1 += W * b.v[3 * gj + 1];
@@ -364,22 +352,23 @@ template <class R> struct PairK {
           key0(I.key0), key1(I.key1) {}
 };
 
-// SDPD force on i from j (Eqs. FijC, FijD, FijR, FijT) written as
+template <class R> struct Z6 {
+    R z0, z1, z2, z3, z4, z5;
+};
+
+// SDPD force on i from j (Eqs. FijC, FijD, FijR, FijT) for a pair already
+// known to lie within h, written as
 //   f = o + ce * e,   o = the part not along e_ij (v_ij, rotational, random),
 // so the torque (-l e) x f = -l e x o needs only o.  with_rt: rotational and
-// random parts (not for pairs with a rigid particle, Section 2.4).  Also
-// returns e, q and 1 - q for the caller's kernel weights.
+// random parts (not for pairs with a rigid particle, Section 2.4).  zmode:
+// 0 draw the six normals into z, 1 use z as given.  Also returns e, q, 1 - q.
 template <class R, class T4>
-__device__ __forceinline__ void sdpd_pair(const PairK<R> &P, const Geo<R> &geo, const T4 &Ai,
-                                          const T4 &Bi, const T4 &Ci, const T4 &Di, const T4 &Aj,
-                                          const T4 &Bj, const T4 &Cj, const T4 &Dj, bool with_rt,
-                                          R &ox, R &oy, R &oz, R &ce, R &ex, R &ey, R &ez, R &q,
-                                          R &om)
+__device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R r2, const T4 &Bi,
+                                          const T4 &Ci, const T4 &Di, const T4 &Bj, const T4 &Cj,
+                                          const T4 &Dj, bool with_rt, int zmode, Z6<R> &z, R &ox,
+                                          R &oy, R &oz, R &ce, R &ex, R &ey, R &ez, R &q, R &om)
 {
     const R third = R(1.0 / 3.0), is2 = R(0.70710678118654752440);
-    R rx, ry, rz;
-    geo.disp(Ai, Aj, rx, ry, rz);
-    const R r2 = rx * rx + ry * ry + rz * rz;
     const R ir = rsqrt_<R>(r2);
     q = r2 * ir * P.irc;
     om = q < R(1) ? R(1) - q : R(0);
@@ -402,15 +391,16 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, const Geo<R> &geo, 
     oz += c3 * (rx * wy - ry * wx);
     // Eq. FijT: (sa S + (sb - sa) tr(S)/3 1) . e / sqrt(dt)
     if (P.noise) {
-        R z0, z1, z2, z3, z4, z5;
-        pair_normals<R>(mir_gid(Di), mir_gid(Dj), P.step, P.key0, P.key1, z0, z1, z2, z3, z4, z5);
+        if (zmode == 0)
+            pair_normals<R>(mir_gid(Di), mir_gid(Dj), P.step, P.key0, P.key1, z.z0, z.z1, z.z2, z.z3,
+                            z.z4, z.z5);
         const R rs = om * Di.z * Dj.z;
         const R sa = P.tn * P.Ka * rs, sb = P.tn * P.Kb * rs;
-        const R sxy = z3 * is2, sxz = z4 * is2, syz = z5 * is2;
-        ce += (sb - sa) * (z0 + z1 + z2) * third;
-        ox += sa * (z0 * ex + sxy * ey + sxz * ez);
-        oy += sa * (sxy * ex + z1 * ey + syz * ez);
-        oz += sa * (sxz * ex + syz * ey + z2 * ez);
+        const R sxy = z.z3 * is2, sxz = z.z4 * is2, syz = z.z5 * is2;
+        ce += (sb - sa) * (z.z0 + z.z1 + z.z2) * third;
+        ox += sa * (z.z0 * ex + sxy * ey + sxz * ez);
+        oy += sa * (sxy * ex + z.z1 * ey + syz * ez);
+        oz += sa * (sxz * ex + syz * ey + z.z2 * ez);
     }
 }
 
@@ -463,9 +453,13 @@ __global__ void __launch_bounds__(128) k_force_fluid(Bufs b)
             jn = __ldg(nb + (long long)(k + 1) * Np);
             An = A[jn]; Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn];
         }
+        R rx, ry, rz, r2;
+        if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) continue;
         const bool rig = mir_type(Aj) == T_RIGID;
         R ox, oy, oz, ce, ex, ey, ez, q, om;
-        sdpd_pair<R>(P, geo, Ai, Bi, Ci, Di, Aj, Bj, Cj, Dj, !rig, ox, oy, oz, ce, ex, ey, ez, q, om);
+        Z6<R> z;
+        sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, !rig, 0, z, ox, oy, oz, ce, ex, ey, ez,
+                     q, om);
         if (rig) {
             // Eq. F_fpi_DG_reac: -F^DG_s W_sj / S_s
             const double4_32a rc = rxn[j];
@@ -484,34 +478,42 @@ __global__ void __launch_bounds__(128) k_force_fluid(Bufs b)
     write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, P.lev);
 }
 
-template <class R> struct Vec2;
-template <> struct Vec2<float> { using T2 = float2; };
-template <> struct Vec2<double> { using T2 = double2; };
-
 // Newton-3 force pass, phase 1: every fluid or wall particle evaluates the
-// pairs of its owned part (partner slot above its own, both non-rigid, at
-// least one fluid) once, stores (f, e x o) in its own column of the pair
-// buffer (coalesced) and keeps its own sum.  Each unordered pair is computed
-// once instead of twice.
+// pairs of its owned part (partner slot above its own, within h, both
+// non-rigid, at least one fluid) once, stores (f, e x o) in its own column of
+// the pair buffer (coalesced) and keeps its own sum.  Each unordered pair is
+// computed once instead of twice.  The first evaluation of a step stores the
+// six normals of each pair; the second reads them back when the list has not
+// been rebuilt in between (same counter, so the same bits).
 template <class R>
-__global__ void __launch_bounds__(128) k_force_half(Bufs b)
+__global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t step = (uint32_t)(*b.step);
+    const bool fill = b.use_cache && velver == 1;
+    const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
+                       *b.cache_step == *b.step;
+    if (fill && s == 0) {
+        *b.cache_epoch = *b.list_epoch;
+        *b.cache_step = *b.step;
+    }
     if (s >= b.N) return;
     const int ti = b.stype[s];
     if (ti == T_RIGID) return;
     const int gi = b.perm[s];
     const Inst &I = b.inst[b.pinst[gi]];
     const Geo<R> geo(I);
-    const PairK<R> P(I, (uint32_t)(*b.step));
+    const PairK<R> P(I, step);
     const T4 *__restrict__ A = Mir<R>::A(b);
     const T4 *__restrict__ Bm = Mir<R>::B(b);
     const T4 *__restrict__ Cm = Mir<R>::C(b);
     const T4 *__restrict__ Dm = Mir<R>::D(b);
     T4 *__restrict__ resA = (T4 *)b.resA;
     T2 *__restrict__ resB = (T2 *)b.resB;
+    T4 *__restrict__ zA = (T4 *)b.zA;
+    T2 *__restrict__ zB = (T2 *)b.zB;
     const int *__restrict__ nb = b.nbr + s;
     const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
     const bool fi = (ti == T_FLUID);
@@ -522,6 +524,7 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b)
     int jn = first < last ? __ldg(nb + (long long)first * Np) : 0;
     T4 An = A[jn], Bn = Bm[jn], Cn = Cm[jn], Dn = Dm[jn];
     for (int k = first; k < last; ++k) {
+        const int j = jn;
         const T4 Aj = An, Bj = Bn, Cj = Cn, Dj = Dn;
         if (k + 1 < last) {
             jn = __ldg(nb + (long long)(k + 1) * Np);
@@ -529,11 +532,39 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b)
         }
         const int tj = mir_type(Aj);
         if (tj == T_RIGID || (!fi && tj != T_FLUID)) continue;
+        const long long at = (long long)(k - first) * Np + s;
+        R rx, ry, rz, r2;
+        if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) {
+            if (fill) {
+                T4 zm;
+                zm.x = R(NAN); zm.y = R(0); zm.z = R(0); zm.w = R(0);
+                zA[at] = zm;
+            }
+            continue;
+        }
+        Z6<R> z;
+        int zmode = 0;
+        if (reuse && P.noise) {
+            const T4 za = zA[at];
+            if (!isnan(za.x)) {
+                const T2 zb = zB[at];
+                z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
+                zmode = 1;
+            }
+        }
         R ox, oy, oz, ce, ex, ey, ez, q, om;
-        sdpd_pair<R>(P, geo, Ai, Bi, Ci, Di, Aj, Bj, Cj, Dj, true, ox, oy, oz, ce, ex, ey, ez, q, om);
+        sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, true, zmode, z, ox, oy, oz, ce, ex, ey,
+                     ez, q, om);
+        if (fill && P.noise) {
+            T4 za;
+            za.x = z.z0; za.y = z.z1; za.z = z.z2; za.w = z.z3;
+            T2 zb;
+            zb.x = z.z4; zb.y = z.z5;
+            zA[at] = za;
+            zB[at] = zb;
+        }
         const R gx = ox + ce * ex, gy = oy + ce * ey, gz = oz + ce * ez;
         const R hx = ey * oz - ez * oy, hy = ez * ox - ex * oz, hz = ex * oy - ey * ox;
-        const long long at = (long long)(k - first) * Np + s;
         T4 ra;
         ra.x = gx; ra.y = gy; ra.z = gz; ra.w = hx;
         T2 rb;
@@ -555,9 +586,10 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b)
 
 // Newton-3 force pass, phase 2 (fluid particles): own sum + the stored
 // results of the pairs owned by lower partners (read through the reverse
-// index; force negated, e x o equal)
-// + the pairs with rigid neighbours evaluated directly (Eqs. FijC, FijD and
-// the drag reaction Eq. F_fpi_DG_reac) + external force.
+// index; force negated, e x o equal; pairs beyond h were never written and
+// are skipped by the same exact test) + the pairs with rigid neighbours
+// evaluated directly (Eqs. FijC, FijD and the drag reaction Eq.
+// F_fpi_DG_reac) + external force.
 template <class R>
 __global__ void __launch_bounds__(128) k_force_gather(Bufs b)
 {
@@ -568,18 +600,18 @@ __global__ void __launch_bounds__(128) k_force_gather(Bufs b)
     if (b.stype[s] != T_FLUID) return;
     const int gi = b.perm[s];
     const Inst &I = b.inst[b.pinst[gi]];
+    const Geo<R> geo(I);
     const T4 *__restrict__ A = Mir<R>::A(b);
     const T4 *__restrict__ resA = (const T4 *)b.resA;
     const T2 *__restrict__ resB = (const T2 *)b.resB;
     const int *__restrict__ nb = b.nbr + s;
+    const T4 Ai = A[s];
     const T4 oa = ((const T4 *)b.ownA)[s];
     const T2 ob = ((const T2 *)b.ownB)[s];
     R fx = oa.x, fy = oa.y, fz = oa.z, tx = oa.w, ty = ob.x, tz = ob.y;
     const int n = b.ncnt[s], first = b.nfirst[s];
     const long long Np = b.Npad;
     const bool any_rigid = b.nbflag[s] & 1;
-    // results of the pairs owned by lower partners, in batches of four so the
-    // scattered loads overlap
     const uint16_t *__restrict__ rv = b.rev + s;
     constexpr int G = 4;
     for (int k0 = 0; k0 < first; k0 += G) {
@@ -590,8 +622,13 @@ __global__ void __launch_bounds__(128) k_force_gather(Bufs b)
             const int k = k0 + g;
             use[g] = k < first;
             const int i = use[g] ? __ldg(nb + (long long)k * Np) : 0;
+            if (use[g]) {
+                const T4 Aj = A[i];
+                R rx, ry, rz, r2;
+                use[g] = (!any_rigid || mir_type(Aj) != T_RIGID) &&
+                         Rel<R>::get(b, I, geo, Ai, Aj, gi, i, rx, ry, rz, r2);
+            }
             at[g] = use[g] ? (long long)__ldg(rv + (long long)k * Np) * Np + i : 0;
-            if (any_rigid && use[g]) use[g] = mir_type(A[i]) != T_RIGID;
         }
         T4 ra[G];
         T2 rb[G];
@@ -611,19 +648,21 @@ __global__ void __launch_bounds__(128) k_force_gather(Bufs b)
     }
     const R lev = K<R>::lever(I);
     if (any_rigid) {
-        const Geo<R> geo(I);
         const PairK<R> P(I, (uint32_t)(*b.step));
         const T4 *__restrict__ Bm = Mir<R>::B(b);
         const T4 *__restrict__ Cm = Mir<R>::C(b);
         const T4 *__restrict__ Dm = Mir<R>::D(b);
-        const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
+        const T4 Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
         for (int k = 0; k < n; ++k) {
             const int j = __ldg(nb + (long long)k * Np);
             const T4 Aj = A[j];
             if (mir_type(Aj) != T_RIGID) continue;
+            R rx, ry, rz, r2;
+            if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) continue;
             R ox, oy, oz, ce, ex, ey, ez, q, om;
-            sdpd_pair<R>(P, geo, Ai, Bi, Ci, Di, Aj, Bm[j], Cm[j], Dm[j], false, ox, oy, oz, ce, ex,
-                         ey, ez, q, om);
+            Z6<R> z;
+            sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bm[j], Cm[j], Dm[j], false, 0, z, ox, oy, oz,
+                         ce, ex, ey, ez, q, om);
             const double4_32a rc = b.rxn[j];
             const R W = P.Wc * (R(1) + R(3) * q) * om * om * om;
             fx += ox + ce * ex - (R)rc.x * W;
@@ -767,9 +806,10 @@ __global__ void k_force_rigid(Bufs b, int velver)
             const int tj = b.type[gj];
             const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
             double rv[3];
-            const double L = sqrt(exact_disp(xi, xj, I, rv));
+            const double r2 = exact_disp(xi, xj, I, rv);
+            const double L = sqrt(r2);
             const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
-            if (tj == T_FLUID && !(e & NB_FAR)) {
+            if (tj == T_FLUID && !(e & NB_FAR) && r2 < I.rc2) {
                 // F^C + F^D of the pair (s, j), summed for Eq. F_fpi_PG
                 const double ex = rv[0] / L, ey = rv[1] / L, ez = rv[2] / L;
                 const double q = L / I.rc, om = 1.0 - q;
@@ -801,7 +841,7 @@ __global__ void k_force_rigid(Bufs b, int velver)
                     dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
                     contact = true;
                     partner = gj;
-                } else if (L < I.rc) {
+                } else if (r2 < I.rc2) {
                     double gap = L - dsum;
                     const double gmin = I.lub_gap_min * dsum;
                     if (gap < gmin) gap = gmin;
@@ -862,15 +902,15 @@ __global__ void k_hist_copy(Bufs b)
 // ---------------------------------------------------------------- launchers
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-void launch_density(const Bufs &b, int precision, int any_filter, cudaStream_t st)
+void launch_density(const Bufs &b, int precision, int any_filter, const int *gate, cudaStream_t st)
 {
     if (!b.N) return;
     if (precision == SDPD_PREC_SPLIT) {
-        k_density<float><<<nblk(b.N, 128), 128, 0, st>>>(b, any_filter);
-        if (any_filter) k_filter<float><<<nblk(b.N, 128), 128, 0, st>>>(b);
+        k_density<float><<<nblk(b.N, 128), 128, 0, st>>>(b, any_filter, gate);
+        if (any_filter) k_filter<float><<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
     } else {
-        k_density<double><<<nblk(b.N, 128), 128, 0, st>>>(b, any_filter);
-        if (any_filter) k_filter<double><<<nblk(b.N, 128), 128, 0, st>>>(b);
+        k_density<double><<<nblk(b.N, 128), 128, 0, st>>>(b, any_filter, gate);
+        if (any_filter) k_filter<double><<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
     }
 }
 
@@ -884,10 +924,10 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
     if (!b.N) return;
     if (newton3) {
         if (precision == SDPD_PREC_SPLIT) {
-            k_force_half<float><<<nblk(b.N, 128), 128, 0, st>>>(b);
+            k_force_half<float><<<nblk(b.N, 128), 128, 0, st>>>(b, velver);
             k_force_gather<float><<<nblk(b.N, 128), 128, 0, st>>>(b);
         } else {
-            k_force_half<double><<<nblk(b.N, 128), 128, 0, st>>>(b);
+            k_force_half<double><<<nblk(b.N, 128), 128, 0, st>>>(b, velver);
             k_force_gather<double><<<nblk(b.N, 128), 128, 0, st>>>(b);
         }
     } else if (precision == SDPD_PREC_SPLIT) {

@@ -51,9 +51,11 @@ __global__ void k_integrate(Bufs b, int velver)
         w[a] = __dadd_rn(b.w[3 * g + a], __dmul_rn(I.hdt, __ddiv_rn(b.T[3 * g + a], iI)));
     }
     if (velver == 1) {
+        double dl[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double xa = __dadd_rn(b.x[3 * g + a], __dmul_rn(I.dt, v[a]));
+            const double x0 = b.x[3 * g + a];
+            double xa = __dadd_rn(x0, __dmul_rn(I.dt, v[a]));
             const double lo = I.origin[a], hi = __dadd_rn(I.origin[a], I.box[a]);
             if (I.periodic[a]) {
                 if (xa < lo) xa = __dadd_rn(xa, I.box[a]);
@@ -65,7 +67,31 @@ __global__ void k_integrate(Bufs b, int velver)
             x[a] = xa;
             b.x[3 * g + a] = xa;
             bad |= !isfinite(xa);
+            // displacement without the periodic jump
+            double d = xa - x0;
+            if (I.periodic[a]) {
+                if (d > 0.5 * I.box[a]) d -= I.box[a];
+                else if (d < -0.5 * I.box[a]) d += I.box[a];
+            }
+            dl[a] = d;
         }
+        // keep the mirrors of the unchanged slot order current: cell-relative
+        // coordinates move by the displacement (the build cell stays), the
+        // displacement since the build decides whether the list still holds
+        double4_32a xl = b.xl64[s], ds = b.dsp[s];
+        xl.x += dl[0]; xl.y += dl[1]; xl.z += dl[2];
+        ds.x += dl[0]; ds.y += dl[1]; ds.z += dl[2];
+        b.xl64[s] = xl;
+        b.dsp[s] = ds;
+        float4 a32 = b.A32[s];
+        a32.x = (float)xl.x; a32.y = (float)xl.y; a32.z = (float)xl.z;
+        b.A32[s] = a32;
+        if (b.A64) {
+            double4_32a a64 = b.A64[s];
+            a64.x = x[0]; a64.y = x[1]; a64.z = x[2];
+            b.A64[s] = a64;
+        }
+        if (ds.x * ds.x + ds.y * ds.y + ds.z * ds.z > I.half_skin * I.half_skin) *b.need_build = 1;
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -150,7 +176,11 @@ __global__ void k_artvis_apply(Bufs b)
     write_vel_mirror<R>(b, s, v, w);
 }
 
-__global__ void k_step_done(long long *step) { *step += 1; }
+__global__ void k_step_done(Bufs b)
+{
+    *b.step += 1;
+    *b.fresh = 0;
+}
 
 // ----------------------------------------------------- viscometer read-out
 // probe layout: [0, nb) velocity sums, [nb, 2nb) counts, [2nb, 2nb+4)
@@ -214,9 +244,12 @@ __global__ void k_count_pairs(Bufs b)
         const int ti = b.stype[s];
         if (ti == T_FLUID || ti == T_RIGID) {
             const int n = b.ncnt[s];
+            const int gi = b.perm[s];
+            const Inst &I = b.inst[b.pinst[gi]];
             for (int k = 0; k < n; ++k) {
                 const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
                 if (e & NB_FAR) continue;
+                if (!exact_within(b, I, gi, b.perm[e])) continue;
                 const int tj = b.stype[e];
                 const bool mj = (tj == T_FLUID || tj == T_RIGID);
                 c += mj ? ((long long)e > s ? 1u : 0u) : 1u;
@@ -226,6 +259,21 @@ __global__ void k_count_pairs(Bufs b)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(b.pair_count, c);
+}
+
+// Flags of the list entries within h at the current positions (exact test).
+__global__ void k_mark_pairs(Bufs b, uint8_t *flags)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.N) return;
+    const int gi = b.perm[s];
+    const Inst &I = b.inst[b.pinst[gi]];
+    const int n = b.ncnt[s];
+    for (int k = 0; k < n; ++k) {
+        const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
+        flags[(long long)k * b.Npad + s] =
+            (!(e & NB_FAR) && exact_within(b, I, gi, b.perm[e & ~NB_FAR])) ? 1 : 0;
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -243,7 +291,7 @@ void launch_integrate(const Bufs &b, int precision, int velver, int any_artvis, 
     }
 }
 
-void launch_step_done(const Bufs &b, cudaStream_t st) { k_step_done<<<1, 1, 0, st>>>(b.step); }
+void launch_step_done(const Bufs &b, cudaStream_t st) { k_step_done<<<1, 1, 0, st>>>(b); }
 
 void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long n)
 {
@@ -258,6 +306,11 @@ void launch_diag(const Bufs &b, int inst, cudaStream_t st, long long n)
     const double big = 1e308;
     cudaMemcpyAsync(&b.probe[7], &big, sizeof(double), cudaMemcpyHostToDevice, st);
     if (n) k_diag<<<nblk(n, 256), 256, 0, st>>>(b, inst);
+}
+
+void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st)
+{
+    if (b.N) k_mark_pairs<<<nblk(b.N, 128), 128, 0, st>>>(b, flags);
 }
 
 void launch_count_pairs(const Bufs &b, cudaStream_t st)
