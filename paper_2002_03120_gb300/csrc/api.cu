@@ -159,8 +159,15 @@ sdpd_status prepare(sdpd_ctx *c)
         const sdpd_params &p = H.P;
         Inst &I = c->inst[k];
         std::memset(&I, 0, sizeof(I));
-        const double rb = p.r_c * (1.0 + c->skin);
-        const double cmin = std::max(rb, 2.0 * H.Rmax + c->skin * p.r_c);
+        // the skin shrinks where a periodic axis could not hold 3 cells with it
+        double skin = c->skin;
+        for (int a = 0; a < 3; ++a)
+            if (p.periodic[a]) {
+                const double room = (p.box[a] / 3.0 - std::max(p.r_c, 2.0 * H.Rmax)) / p.r_c;
+                skin = std::min(skin, std::max(0.0, room * 0.999));
+            }
+        const double rb = p.r_c * (1.0 + skin);
+        const double cmin = std::max(rb, 2.0 * H.Rmax + skin * p.r_c);
         for (int a = 0; a < 3; ++a) {
             I.origin[a] = p.origin[a];
             I.box[a] = p.box[a];
@@ -247,7 +254,7 @@ sdpd_status prepare(sdpd_ctx *c)
         I.lever_fluidf = (float)I.lever_fluid;
         I.rb = rb;
         I.rb2 = rb * rb;
-        I.half_skin = 0.5 * c->skin * h;
+        I.half_skin = 0.5 * skin * h;
         I.rb2f = (float)(rb * rb * (1.0 + 1e-5));
         I.guard_lo = (float)(I.rc2 * (1.0 - 1e-5));
         I.guard_hi = (float)(I.rc2 * (1.0 + 1e-5));

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter, const i
             if (e & NB_FAR) continue;
             R rx, ry, rz, r2;
             if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
-            const R q = sqrt(r2) * irc;
+            const R q = r2 * rsqrt_<R>(r2) * irc;
             const R om = q < R(1) ? R(1) - q : R(0);
             acc.add(Wc * (R(1) + R(3) * q) * om * om * om);
         }
@@ -535,11 +535,11 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
         const long long at = (long long)(k - first) * Np + s;
         R rx, ry, rz, r2;
         if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) {
-            if (fill) {
-                T4 zm;
-                zm.x = R(NAN); zm.y = R(0); zm.z = R(0); zm.w = R(0);
-                zA[at] = zm;
-            }
+            // beyond h: marked for the partner's gather and the normals cache
+            T4 nm;
+            nm.x = R(NAN); nm.y = R(0); nm.z = R(0); nm.w = R(0);
+            resA[at] = nm;
+            if (fill) zA[at] = nm;
             continue;
         }
         Z6<R> z;
@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
 
 // Newton-3 force pass, phase 2 (fluid particles): own sum + the stored
 // results of the pairs owned by lower partners (read through the reverse
-// index; force negated, e x o equal; pairs beyond h were never written and
-// are skipped by the same exact test) + the pairs with rigid neighbours
+// index; force negated, e x o equal; pairs the owner found beyond h carry a
+// NaN marker) + the pairs with rigid neighbours
 // evaluated directly (Eqs. FijC, FijD and the drag reaction Eq.
 // F_fpi_DG_reac) + external force.
 template <class R>
@@ -622,12 +622,7 @@ __global__ void __launch_bounds__(128) k_force_gather(Bufs b)
             const int k = k0 + g;
             use[g] = k < first;
             const int i = use[g] ? __ldg(nb + (long long)k * Np) : 0;
-            if (use[g]) {
-                const T4 Aj = A[i];
-                R rx, ry, rz, r2;
-                use[g] = (!any_rigid || mir_type(Aj) != T_RIGID) &&
-                         Rel<R>::get(b, I, geo, Ai, Aj, gi, i, rx, ry, rz, r2);
-            }
+            if (use[g] && any_rigid) use[g] = mir_type(A[i]) != T_RIGID;
             at[g] = use[g] ? (long long)__ldg(rv + (long long)k * Np) * Np + i : 0;
         }
         T4 ra[G];
@@ -641,7 +636,8 @@ __global__ void __launch_bounds__(128) k_force_gather(Bufs b)
         }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            if (!use[g]) continue;
+            // NaN marks a pair beyond h (written by the owner)
+            if (!use[g] || isnan(ra[g].x)) continue;
             fx -= ra[g].x; fy -= ra[g].y; fz -= ra[g].z;
             tx += ra[g].w; ty += rb[g].x; tz += rb[g].y;
         }
