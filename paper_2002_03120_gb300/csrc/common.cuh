@@ -80,11 +80,11 @@ struct Bufs {
     double4_32a *A64, *B64, *C64, *D64;
     int *stype;
     double *sd, *sp, *sp2;     // density, pressure (raw / filtered) per slot
-    // neighbour list (each list ascending in slot); nfirst = entries below the
-    // particle's own slot; rev = position of the pair in the lower partner's
-    // owned part (Newton-3 pass)
-    int *nbr, *ncnt, *nfirst;
-    uint16_t *rev;             // entry k of s below s -> position of s in the partner's owned part
+    // neighbour lists: owned pairs first (Newton-3 ownership), see k_neighbors
+    int *nbr, *ncnt, *nfirst;  // nfirst = length of the owned prefix
+    int *hw, *hsplit;          // owned prefix runs: [0,hw) home cell after s, [hw,hsplit) home wrap, [hsplit,nfirst) higher cells
+    int *skey;                 // cell key per slot
+    uint16_t *rev;             // non-owned entry k of s -> position of s in the partner's list
     uint8_t *nbflag;           // per slot: bit 0 = has a rigid neighbour
     int capown;                // owned entries per particle in the pair buffer
     void *resA, *resB;         // pair results [capown][Npad]: R4 {f, t.x}, R2 {t.y, t.z}

@@ -175,6 +175,7 @@ __global__ void k_gather(Bufs b, int precision, const int *gate)
         }
         b.A32[s] = make_float4((float)xl[0], (float)xl[1], (float)xl[2],
                                __uint_as_float(pack_cell(t, c[0], c[1], c[2])));
+        b.skey[s] = b.key[g];
         b.xl64[s] = make_double4_32a(xl[0], xl[1], xl[2], 0.0);
         b.dsp[s] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     }
@@ -194,10 +195,48 @@ __global__ void k_gather(Bufs b, int precision, const int *gate)
 
 // Neighbour list of particle (slot) s: candidates from the cells around s's
 // cell (cells are at least max(rb, largest sphere diameter + skin) wide,
-// periodic axes at least 3 cells), visited in ascending key order so the list
-// comes out ascending in slot.  A pair is listed when r < rb (float test: the
-// list only has to be a superset of the pairs within h), or when both are
+// periodic axes at least 3 cells).  A pair is listed when r < rb (float test:
+// the list only has to be a superset of the pairs within h), or when both are
 // rigid and r < R_i + R_j + skin h (contact range; flagged NB_FAR).
+//
+// Newton-3 ownership, balanced across the particles of a cell: a pair in two
+// cells belongs to the particle in the cell of higher key; inside a cell of m
+// particles, particle a owns the cell-mates b at cyclic distance
+// d = (b - a) mod m below m/2 (d = m/2: the lower slot).  The list is written
+// as [home owned, cyclic from s+1][higher cells][home rest][lower cells], so
+// the owned pairs form the prefix [0, nfirst); the runs [0, hw) (home, slots
+// above s), [hw, hsplit) (home, wrapped) and [hsplit, nfirst) (higher cells)
+// are each ascending in slot, which the reverse index searches.
+struct NbWriter {
+    const Bufs &b;
+    long long s, Np;
+    int cnt;
+    bool rig;
+    __device__ __forceinline__ void put(uint32_t entry, int tj)
+    {
+        if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
+        ++cnt;
+        rig |= (tj == T_RIGID);
+    }
+};
+
+__device__ __forceinline__ bool nb_test(const Bufs &b, const Inst &I, const float4 &Ai, int ti, float Ri,
+                                        int j, float sx, float sy, float sz, uint32_t &entry, int &tj)
+{
+    const float4 Aj = b.A32[j];
+    tj = unpack_type(__float_as_uint(Aj.w));
+    const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy, dz = (Ai.z - Aj.z) - sz;
+    const float r2f = dx * dx + dy * dy + dz * dz;
+    entry = (uint32_t)j;
+    if (r2f < I.rb2f) return true;
+    if (ti == T_RIGID && tj == T_RIGID) {
+        const float lim = (Ri + (float)b.R[b.perm[j]] + (float)(2.0 * I.half_skin)) * 1.0001f;
+        entry |= NB_FAR;
+        return r2f < lim * lim;
+    }
+    return false;
+}
+
 __global__ void k_neighbors(Bufs b, const int *gate)
 {
     GATE;
@@ -208,57 +247,62 @@ __global__ void k_neighbors(Bufs b, const int *gate)
     const int ti = b.stype[s];
     const float Ri = (ti == T_RIGID) ? (float)b.R[gi] : 0.f;
     const float4 Ai = b.A32[s];
-    const uint32_t bits = __float_as_uint(Ai.w);
-    const int key_i =
-        I.cell_base + b.cell_rank[I.cell_base + (unpack_cz(bits) * I.nc[1] + unpack_cy(bits)) * I.nc[0] + unpack_cx(bits)];
+    const int key_i = b.skey[s];
     const int *adj = b.cell_adj + (long long)key_i * 27;
-    const float rbf = I.rb2f;
-    const float skinr = (float)(2.0 * I.half_skin);
-    int cnt = 0, nlow = 0;
-    bool rig = false;
-    const long long Np = b.Npad;
-    for (int q = 0; q < 27; ++q) {
-        const int code = adj[q];
-        if (code < 0) break;
-        const int key = code >> 5, oc = code & 31;
-        const int ox = oc % 3 - 1, oy = (oc / 3) % 3 - 1, oz = oc / 9 - 1;
-        const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
-        // shift of the neighbour cell in whole cells (periodic image)
-        const float sx = (float)ox * I.csf[0], sy = (float)oy * I.csf[1], sz = (float)oz * I.csf[2];
-        for (int j = j0; j < j1; ++j) {
-            if (j == s) continue;
-            const float4 Aj = b.A32[j];
-            const int tj = unpack_type(__float_as_uint(Aj.w));
-            const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy, dz = (Ai.z - Aj.z) - sz;
-            const float r2f = dx * dx + dy * dy + dz * dz;
-            uint32_t entry = (uint32_t)j;
-            bool in = r2f < rbf;
-            if (!in && ti == T_RIGID && tj == T_RIGID) {
-                const float lim = (Ri + (float)b.R[b.perm[j]] + skinr) * 1.0001f;
-                in = r2f < lim * lim;
-                entry |= NB_FAR;
-            }
-            if (in) {
-                if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
-                ++cnt;
-                nlow += (j < s);
-                rig |= (tj == T_RIGID);
+    const int c0 = b.cstart[key_i], c1 = b.cstart[key_i + 1], m = c1 - c0;
+    NbWriter W{ b, s, b.Npad, 0, false };
+    uint32_t entry;
+    int tj;
+    // 1: home cell, owned part, cyclic from s + 1
+    int d = 1, hw = 0;
+    for (; d < m; ++d) {
+        const int j = c0 + (int)((s - c0 + d) % m);
+        const bool owned = (2 * d < m) || (2 * d == m && s < j);
+        if (!owned) break;
+        if (nb_test(b, I, Ai, ti, Ri, j, 0.f, 0.f, 0.f, entry, tj)) {
+            W.put(entry, tj);
+            hw += (j > s);
+        }
+    }
+    const int hsplit = W.cnt;
+    // 2: cells of higher key, 3: the rest of the home cell, 4: lower keys
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int q = 0; q < 27; ++q) {
+            const int code = adj[q];
+            if (code < 0) break;
+            const int key = code >> 5;
+            if (pass == 0 ? key <= key_i : key >= key_i) continue;
+            const int oc = code & 31;
+            const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
+                        sz = (float)(oc / 9 - 1) * I.csf[2];
+            const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
+            for (int j = j0; j < j1; ++j)
+                if (nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) W.put(entry, tj);
+        }
+        if (pass == 0) {
+            const int own = W.cnt;
+            b.nfirst[s] = own < b.cap ? own : b.cap;
+            for (; d < m; ++d) {
+                const int j = c0 + (int)((s - c0 + d) % m);
+                if (nb_test(b, I, Ai, ti, Ri, j, 0.f, 0.f, 0.f, entry, tj)) W.put(entry, tj);
             }
         }
     }
+    int cnt = W.cnt;
     if (cnt > b.cap) {
         atomicOr(b.err, ERR_NBR_CAP);
         cnt = b.cap;
     }
     b.ncnt[s] = cnt;
-    b.nfirst[s] = nlow < b.cap ? nlow : b.cap;
-    b.nbflag[s] = rig ? 1 : 0;
+    b.hw[s] = hw;
+    b.hsplit[s] = hsplit < b.cap ? hsplit : b.cap;
+    b.nbflag[s] = W.rig ? 1 : 0;
 }
 
-// For every entry of s's list below s (partner i < s), the position of s in
-// the owned (upper) part of i's list, by binary search (lists are ascending);
-// four searches run interleaved so their loads overlap.  The Newton-3 force
-// pass reads the pair result from there.
+// For every non-owned entry of s (positions [nfirst, n)), the position of s
+// in the partner's owned prefix: in its home run above it or its wrapped home
+// run (same cell) or its higher-cell run (partner in a lower cell); each run
+// is ascending, so a binary search finds it.  Four searches run interleaved.
 __device__ __forceinline__ int nb_at(const Bufs &b, int i, int k)
 {
     return (int)((uint32_t)__ldg(b.nbr + (long long)k * b.Npad + i) & ~NB_FAR);
@@ -270,19 +314,30 @@ __global__ void k_rev(Bufs b, const int *gate)
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     const long long Np = b.Npad;
-    const int first = b.nfirst[s];
-    if (b.ncnt[s] - first > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+    const int first = b.nfirst[s], n = b.ncnt[s];
+    const int ks = b.skey[s];
     constexpr int G = 4;
-    for (int k0 = 0; k0 < first; k0 += G) {
-        int part[G], lo[G], hi[G], f0[G];
+    for (int k0 = first; k0 < n; k0 += G) {
+        int part[G], lo[G], hi[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int k = k0 + g;
-            part[g] = k < first ? (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR) : -1;
-            lo[g] = part[g] >= 0 ? b.nfirst[part[g]] : 0;
-            hi[g] = part[g] >= 0 ? b.ncnt[part[g]] : 0;
-            f0[g] = lo[g];
+            part[g] = k < n ? (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR) : -1;
+            lo[g] = hi[g] = 0;
+            if (part[g] >= 0) {
+                const int i = part[g];
+                if (b.skey[i] == ks) {
+                    if (s > i) { lo[g] = 0; hi[g] = b.hw[i]; }
+                    else { lo[g] = b.hw[i]; hi[g] = b.hsplit[i]; }
+                } else {
+                    lo[g] = b.hsplit[i];
+                    hi[g] = b.nfirst[i];
+                }
+            }
         }
+        int end[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) end[g] = hi[g];
         bool active = true;
         while (active) {
             active = false;
@@ -299,10 +354,10 @@ __global__ void k_rev(Bufs b, const int *gate)
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int k = k0 + g;
-            if (k >= first) break;
-            const bool ok = lo[g] < b.ncnt[part[g]] && nb_at(b, part[g], lo[g]) == (int)s;
+            if (k >= n) break;
+            const bool ok = lo[g] < end[g] && nb_at(b, part[g], lo[g]) == (int)s;
             if (!ok) atomicOr(b.err, ERR_REV);
-            b.rev[(long long)k * Np + s] = (uint16_t)(ok ? lo[g] - f0[g] : 0);
+            b.rev[(long long)k * Np + s] = (uint16_t)(ok ? lo[g] : 0);
         }
     }
 }

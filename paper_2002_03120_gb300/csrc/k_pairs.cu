@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter, const i
             if (e & NB_FAR) continue;
             R rx, ry, rz, r2;
             if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
-            const R q = r2 * rsqrt_<R>(r2) * irc;
+            // float: correctly rounded sqrt; double: r2 / sqrt via rsqrt (~1 ulp)
+            const R q = (sizeof(R) == 4 ? sqrt(r2) : r2 * rsqrt_<R>(r2)) * irc;
             const R om = q < R(1) ? R(1) - q : R(0);
             acc.add(Wc * (R(1) + R(3) * q) * om * om * om);
         }
@@ -479,9 +480,9 @@ __global__ void __launch_bounds__(128) k_force_fluid(Bufs b)
 }
 
 // Newton-3 force pass, phase 1: every fluid or wall particle evaluates the
-// pairs of its owned part (partner slot above its own, within h, both
-// non-rigid, at least one fluid) once, stores (f, e x o) in its own column of
-// the pair buffer (coalesced) and keeps its own sum.  Each unordered pair is
+// pairs of its owned prefix (see k_neighbors; within h, both non-rigid, at
+// least one fluid) once, stores (f, e x o) in its own column of the pair
+// buffer (coalesced) and keeps its own sum.  Each unordered pair is
 // computed once instead of twice.  The first evaluation of a step stores the
 // six normals of each pair; the second reads them back when the list has not
 // been rebuilt in between (same counter, so the same bits).
@@ -518,12 +519,11 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
     const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
     const bool fi = (ti == T_FLUID);
     R fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0;
-    const int n = b.ncnt[s], first = b.nfirst[s];
-    const int last = min(n, first + b.capown);
+    const int last = b.nfirst[s];  // the owned prefix of the list
     const long long Np = b.Npad;
-    int jn = first < last ? __ldg(nb + (long long)first * Np) : 0;
+    int jn = 0 < last ? __ldg(nb) : 0;
     T4 An = A[jn], Bn = Bm[jn], Cn = Cm[jn], Dn = Dm[jn];
-    for (int k = first; k < last; ++k) {
+    for (int k = 0; k < last; ++k) {
         const int j = jn;
         const T4 Aj = An, Bj = Bn, Cj = Cn, Dj = Dn;
         if (k + 1 < last) {
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
         }
         const int tj = mir_type(Aj);
         if (tj == T_RIGID || (!fi && tj != T_FLUID)) continue;
-        const long long at = (long long)(k - first) * Np + s;
+        const long long at = (long long)k * Np + s;
         R rx, ry, rz, r2;
         if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) {
             // beyond h: marked for the partner's gather and the normals cache
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
 }
 
 // Newton-3 force pass, phase 2 (fluid particles): own sum + the stored
-// results of the pairs owned by lower partners (read through the reverse
+// results of the pairs its partners own (read through the reverse
 // index; force negated, e x o equal; pairs the owner found beyond h carry a
 // NaN marker) + the pairs with rigid neighbours
 // evaluated directly (Eqs. FijC, FijD and the drag reaction Eq.
@@ -614,13 +614,13 @@ __global__ void __launch_bounds__(128) k_force_gather(Bufs b)
     const bool any_rigid = b.nbflag[s] & 1;
     const uint16_t *__restrict__ rv = b.rev + s;
     constexpr int G = 4;
-    for (int k0 = 0; k0 < first; k0 += G) {
+    for (int k0 = first; k0 < n; k0 += G) {
         long long at[G];
         bool use[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int k = k0 + g;
-            use[g] = k < first;
+            use[g] = k < n;
             const int i = use[g] ? __ldg(nb + (long long)k * Np) : 0;
             if (use[g] && any_rigid) use[g] = mir_type(A[i]) != T_RIGID;
             at[g] = use[g] ? (long long)__ldg(rv + (long long)k * Np) * Np + i : 0;
