@@ -455,7 +455,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     IALLOC(b.nbr, (size_t)c->cap * c->Npad);
     IALLOC(b.ncnt, N);
     IALLOC(b.nfirst, N);
-    IALLOC(b.hw, N); IALLOC(b.hsplit, N); IALLOC(b.skey, N);
+    IALLOC(b.skey, N);
     IALLOC(b.nbflag, N);
     IALLOC(b.rev, (size_t)c->cap * c->Npad);
     b.capown = c->cap;

@@ -82,7 +82,6 @@ struct Bufs {
     double *sd, *sp, *sp2;     // density, pressure (raw / filtered) per slot
     // neighbour lists: owned pairs first (Newton-3 ownership), see k_neighbors
     int *nbr, *ncnt, *nfirst;  // nfirst = length of the owned prefix
-    int *hw, *hsplit;          // owned prefix runs: [0,hw) home cell after s, [hw,hsplit) home wrap, [hsplit,nfirst) higher cells
     int *skey;                 // cell key per slot
     uint16_t *rev;             // non-owned entry k of s -> position of s in the partner's list
     uint8_t *nbflag;           // per slot: bit 0 = has a rigid neighbour

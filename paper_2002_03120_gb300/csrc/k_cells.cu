@@ -199,14 +199,20 @@ __global__ void k_gather(Bufs b, int precision, const int *gate)
 // the list only has to be a superset of the pairs within h), or when both are
 // rigid and r < R_i + R_j + skin h (contact range; flagged NB_FAR).
 //
-// Newton-3 ownership, balanced across the particles of a cell: a pair in two
-// cells belongs to the particle in the cell of higher key; inside a cell of m
-// particles, particle a owns the cell-mates b at cyclic distance
-// d = (b - a) mod m below m/2 (d = m/2: the lower slot).  The list is written
-// as [home owned, cyclic from s+1][higher cells][home rest][lower cells], so
-// the owned pairs form the prefix [0, nfirst); the runs [0, hw) (home, slots
-// above s), [hw, hsplit) (home, wrapped) and [hsplit, nfirst) (higher cells)
-// are each ascending in slot, which the reverse index searches.
+// Newton-3 ownership, balanced so that every particle owns about half of its
+// pairs whatever its position in the cell: the pair of slots a < b belongs to
+// a when bit 15 of the hash (a * 0x9E3779B1) ^ (b * 0x85EBCA77) is set, else
+// to b.  The list is written as [owned][not owned], each part ascending in
+// slot (cells visited in ascending key), so the owned pairs are the prefix
+// [0, nfirst) and a partner's position is found by binary search in it.
+__device__ __forceinline__ bool pair_owned(long long s, int j)
+{
+    const uint32_t lo = (uint32_t)min((long long)j, s), hi = (uint32_t)max((long long)j, s);
+    const uint32_t h = (lo * 0x9E3779B1u) ^ (hi * 0x85EBCA77u);
+    const bool low_owns = (h >> 15) & 1u;
+    return low_owns == (s < j);
+}
+
 struct NbWriter {
     const Bufs &b;
     long long s, Np;
@@ -247,46 +253,25 @@ __global__ void k_neighbors(Bufs b, const int *gate)
     const int ti = b.stype[s];
     const float Ri = (ti == T_RIGID) ? (float)b.R[gi] : 0.f;
     const float4 Ai = b.A32[s];
-    const int key_i = b.skey[s];
-    const int *adj = b.cell_adj + (long long)key_i * 27;
-    const int c0 = b.cstart[key_i], c1 = b.cstart[key_i + 1], m = c1 - c0;
+    const int *adj = b.cell_adj + (long long)b.skey[s] * 27;
     NbWriter W{ b, s, b.Npad, 0, false };
     uint32_t entry;
     int tj;
-    // 1: home cell, owned part, cyclic from s + 1
-    int d = 1, hw = 0;
-    for (; d < m; ++d) {
-        const int j = c0 + (int)((s - c0 + d) % m);
-        const bool owned = (2 * d < m) || (2 * d == m && s < j);
-        if (!owned) break;
-        if (nb_test(b, I, Ai, ti, Ri, j, 0.f, 0.f, 0.f, entry, tj)) {
-            W.put(entry, tj);
-            hw += (j > s);
-        }
-    }
-    const int hsplit = W.cnt;
-    // 2: cells of higher key, 3: the rest of the home cell, 4: lower keys
     for (int pass = 0; pass < 2; ++pass) {
+        const bool want_owned = (pass == 0);
         for (int q = 0; q < 27; ++q) {
             const int code = adj[q];
             if (code < 0) break;
-            const int key = code >> 5;
-            if (pass == 0 ? key <= key_i : key >= key_i) continue;
-            const int oc = code & 31;
+            const int key = code >> 5, oc = code & 31;
             const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
                         sz = (float)(oc / 9 - 1) * I.csf[2];
             const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
-            for (int j = j0; j < j1; ++j)
+            for (int j = j0; j < j1; ++j) {
+                if (j == s || pair_owned(s, j) != want_owned) continue;
                 if (nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) W.put(entry, tj);
-        }
-        if (pass == 0) {
-            const int own = W.cnt;
-            b.nfirst[s] = own < b.cap ? own : b.cap;
-            for (; d < m; ++d) {
-                const int j = c0 + (int)((s - c0 + d) % m);
-                if (nb_test(b, I, Ai, ti, Ri, j, 0.f, 0.f, 0.f, entry, tj)) W.put(entry, tj);
             }
         }
+        if (pass == 0) b.nfirst[s] = W.cnt < b.cap ? W.cnt : b.cap;
     }
     int cnt = W.cnt;
     if (cnt > b.cap) {
@@ -294,15 +279,12 @@ __global__ void k_neighbors(Bufs b, const int *gate)
         cnt = b.cap;
     }
     b.ncnt[s] = cnt;
-    b.hw[s] = hw;
-    b.hsplit[s] = hsplit < b.cap ? hsplit : b.cap;
     b.nbflag[s] = W.rig ? 1 : 0;
 }
 
 // For every non-owned entry of s (positions [nfirst, n)), the position of s
-// in the partner's owned prefix: in its home run above it or its wrapped home
-// run (same cell) or its higher-cell run (partner in a lower cell); each run
-// is ascending, so a binary search finds it.  Four searches run interleaved.
+// in the partner's owned prefix (ascending), by binary search; four searches
+// run interleaved so their loads overlap.
 __device__ __forceinline__ int nb_at(const Bufs &b, int i, int k)
 {
     return (int)((uint32_t)__ldg(b.nbr + (long long)k * b.Npad + i) & ~NB_FAR);
@@ -315,7 +297,6 @@ __global__ void k_rev(Bufs b, const int *gate)
     if (s >= b.N) return;
     const long long Np = b.Npad;
     const int first = b.nfirst[s], n = b.ncnt[s];
-    const int ks = b.skey[s];
     constexpr int G = 4;
     for (int k0 = first; k0 < n; k0 += G) {
         int part[G], lo[G], hi[G];
@@ -323,17 +304,8 @@ __global__ void k_rev(Bufs b, const int *gate)
         for (int g = 0; g < G; ++g) {
             const int k = k0 + g;
             part[g] = k < n ? (int)((uint32_t)b.nbr[(long long)k * Np + s] & ~NB_FAR) : -1;
-            lo[g] = hi[g] = 0;
-            if (part[g] >= 0) {
-                const int i = part[g];
-                if (b.skey[i] == ks) {
-                    if (s > i) { lo[g] = 0; hi[g] = b.hw[i]; }
-                    else { lo[g] = b.hw[i]; hi[g] = b.hsplit[i]; }
-                } else {
-                    lo[g] = b.hsplit[i];
-                    hi[g] = b.nfirst[i];
-                }
-            }
+            lo[g] = 0;
+            hi[g] = part[g] >= 0 ? b.nfirst[part[g]] : 0;
         }
         int end[G];
 #pragma unroll

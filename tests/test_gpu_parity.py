@@ -65,7 +65,8 @@ def test_density_pressure_forces(name, precision):
     orc = _oracle_eval(case, step=3)
     g = sim.state()
     o = orc.state()
-    tol_d = 1e-12 if precision == B.SDPD_PREC_FP64 else 1e-7
+    # split: float kernel values (a few ulp each) under a compensated sum
+    tol_d = 1e-12 if precision == B.SDPD_PREC_FP64 else 1e-6
     assert rel_l2(g["d"], o["d"]) < tol_d
     # pressure is a small difference of large terms: judged against p0
     p0 = case["params"]["p0"]
