@@ -200,14 +200,15 @@ __global__ void k_gather(Bufs b, int precision, const int *gate)
 // rigid and r < R_i + R_j + skin h (contact range; flagged NB_FAR).
 //
 // Newton-3 ownership, balanced so that every particle owns about half of its
-// pairs whatever its position in the cell: the pair of slots a < b belongs to
-// a when bit 15 of the hash (a * 0x9E3779B1) ^ (b * 0x85EBCA77) is set, else
-// to b.  The list is written as [owned][not owned], each part ascending in
+// pairs whatever its position in the cell: the pair of instance-local slots
+// a < b belongs to a when bit 15 of the hash (a * 0x9E3779B1) ^
+// (b * 0x85EBCA77) is set, else to b.  The list is written as [owned][not owned], each part ascending in
 // slot (cells visited in ascending key), so the owned pairs are the prefix
 // [0, nfirst) and a partner's position is found by binary search in it.
-__device__ __forceinline__ bool pair_owned(long long s, int j)
+__device__ __forceinline__ bool pair_owned(long long s, int j, int base)
 {
-    const uint32_t lo = (uint32_t)min((long long)j, s), hi = (uint32_t)max((long long)j, s);
+    // instance-local slots: an instance owns the same pairs alone or batched
+    const uint32_t lo = (uint32_t)(min((long long)j, s) - base), hi = (uint32_t)(max((long long)j, s) - base);
     const uint32_t h = (lo * 0x9E3779B1u) ^ (hi * 0x85EBCA77u);
     const bool low_owns = (h >> 15) & 1u;
     return low_owns == (s < j);
@@ -254,6 +255,7 @@ __global__ void k_neighbors(Bufs b, const int *gate)
     const float Ri = (ti == T_RIGID) ? (float)b.R[gi] : 0.f;
     const float4 Ai = b.A32[s];
     const int *adj = b.cell_adj + (long long)b.skey[s] * 27;
+    const int base = b.cstart[I.cell_base];  // first slot of the instance
     NbWriter W{ b, s, b.Npad, 0, false };
     uint32_t entry;
     int tj;
@@ -267,7 +269,7 @@ __global__ void k_neighbors(Bufs b, const int *gate)
                         sz = (float)(oc / 9 - 1) * I.csf[2];
             const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
             for (int j = j0; j < j1; ++j) {
-                if (j == s || pair_owned(s, j) != want_owned) continue;
+                if (j == s || pair_owned(s, j, base) != want_owned) continue;
                 if (nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) W.put(entry, tj);
             }
         }
