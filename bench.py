@@ -36,10 +36,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SDPD-DEM pair updates/s & timesteps/s on 1 GB300, vs plain FP64 GPU path"
 UNIT = "pair updates/s"
-WORKLOAD = "single-particle sedimentation 32x32x64 (65,535 fluid + 1 sphere + 8,192 wall)"
-# algorithmic FP64 flops per ordered fluid pair evaluation of the force pass
+WORKLOADS = {
+    "sedimentation": "single-particle sedimentation 32x32x64 (65,535 fluid + 1 sphere + 8,192 wall)",
+    "poiseuille": "reverse-Poiseuille 16x32x16 (8,192 fluid), fully periodic",
+    "dambreak": "dam break 126x63x63 column (490,094 fluid + 10,000 spheres + 501,903 wall)",
+    "batch": "batched viscometer sweep: 64 slurry instances, N_f log-uniform 20k-400k",
+}
+# algorithmic flops of one evaluation of one unordered pair by the force pass
 # (Eqs. FijC, FijD, FijR, FijT incl. Box-Muller; transcendentals counted as 1)
 FLOPS_PER_PAIR = 160.0
+# nominal ALU peaks from unit counts x maximum SM clock (152 SMs, 2070 MHz):
+# FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM, 2 flops per FMA
+FP64_PEAK_TF = 152 * 2 * 2 * 2070e6 / 1e12
+FP32_PEAK_TF = 152 * 128 * 2 * 2070e6 / 1e12
 
 
 def parse():
@@ -50,6 +59,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sedimentation", choices=sorted(WORKLOADS))
     return ap.parse_args()
 
 
@@ -60,9 +70,15 @@ def dist_env():
     return ws, rank, local
 
 
-def make_case():
+def make_case(workload="sedimentation"):
     from paper_2002_03120_gb300 import cases
-    return cases.sedimentation()
+    if workload == "sedimentation":
+        return cases.sedimentation()
+    if workload == "poiseuille":
+        return cases.poiseuille_si()
+    if workload == "dambreak":
+        return cases.dam_break()
+    return cases.viscometer_batch()
 
 
 # ------------------------------------------------------------------ clocks
@@ -125,7 +141,7 @@ def time_native(args, ws, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
-    case = make_case()
+    case = make_case(args.workload)
     prec = B.SDPD_PREC_FP64 if args.precision == "fp64" else B.SDPD_PREC_SPLIT
 
     def run_path(precision):
@@ -240,6 +256,29 @@ def _oracle_pairs(sim, case):
     return int(np.sum(mob[ij[:, 0]] | mob[ij[:, 1]]))
 
 
+def ncu_counters():
+    """ncu counters of the profiled force kernels (profiles/), used only while
+    the kernel source is the one that was profiled."""
+    import hashlib
+    try:
+        c = json.load(open(os.path.join(ROOT, "profiles", "counters_sedimentation.json")))
+        src = open(os.path.join(ROOT, c["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != c["source_sha256_16"]:
+            return {}
+        return c
+    except Exception:
+        return {}
+
+
+def pipe_util(c, fp64):
+    if not c:
+        return None
+    if fp64:
+        return {"fp64_pipe": c["fp64_pipe_pct"] / 100.0, "lanes_active": c["threads_per_inst"] / 32.0}
+    return {"fma_pipe": c["fma_pipe_pct"] / 100.0, "alu_pipe": c["alu_pipe_pct"] / 100.0,
+            "issue_active": c["issue_active_pct"] / 100.0, "lanes_active": c["threads_per_inst"] / 32.0}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -277,7 +316,7 @@ def main():
             "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "data": "synthetic", "config": {"workload": WORKLOADS["sedimentation"], "sample": sample},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
@@ -289,36 +328,49 @@ def main():
     steps_per_s = args.steps / (t_max / 1e3)
     other_val = other_r["pairs"] * 2 * args.steps / (other_r["ms"] / 1e3)
     peaks = measured_peaks()
-    # dominant kernel: the fluid force pass; FP64 ALU bound
-    force_flops = FLOPS_PER_PAIR * 2 * pairs  # ordered pairs ~ 2 x unordered
+    cnt = ncu_counters()
+    fp64 = args.precision == "fp64"
+    # dominant kernel: the force pass (k_force_half + k_force_gather + the
+    # sphere kernel), ALU bound; algorithmic flops = 160 per unordered pair
+    force_flops = FLOPS_PER_PAIR * pairs
     achieved_tf = force_flops / (main_r["force_ms"] / 1e3) / 1e12
-    sm_mhz = main_r["clocks"].get("sm_mhz") or 1440.0
-    # FP64 peak: 152 SMs x 2 DFMA/clk/SM (nominal 1.25 TFLOP/s at 2070 MHz), 2 flops per DFMA
-    fp64_peak_tf = 152 * 2 * 2 * 2070e6 / 1e12
+    other_tf = FLOPS_PER_PAIR * other_r["pairs"] / (other_r["force_ms"] / 1e3) / 1e12
+    kd, kf = "k_force_half<double>", "k_force_half<float>"
+    main_k, other_k = (kd, kf) if fp64 else (kf, kd)
+    fp64_peak_tf = FP64_PEAK_TF if fp64 else FP32_PEAK_TF
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32 pairs / f64 state",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": main_r["N"], "pairs_per_eval": pairs,
+        "config": {"workload": WORKLOADS[args.workload], "particles": main_r["N"], "pairs_per_eval": pairs,
                    "evals_per_step": 2, "precision": args.precision,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{ws}"},
         "timesteps_per_s": steps_per_s,
         "gpu_launches": main_r["kernels"] * args.steps,
         "clocks": main_r["clocks"],
-        "roofline": {"kernel": "k_force_fluid (force pass, velver 1)", "bound": "alu",
-                     "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp64_peak_tf, "traffic": None,
+        "roofline": {"kernel": "force pass (k_force_half + k_force_gather + k_force_rigid), velver 1",
+                     "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp64_peak_tf,
+                     "traffic": cnt.get(main_k, {}).get("dram_bytes_per_launch"),
                      "ms_per_launch": main_r["force_ms"],
-                     "note": "FP64 peak from unit counts x max clock (nominal)"},
+                     "pipe_util_ncu": pipe_util(cnt.get(main_k), fp64),
+                     "note": ("peak = %s nominal from unit counts x max clock (2070 MHz); "
+                              "achieved counts 160 flop per unordered pair; traffic = ncu DRAM "
+                              "bytes of %s per launch (profiles/)") % ("FP64" if fp64 else "FP32", main_k)},
         "e2e": {"value": pairs * 2 / (main_r["e2e_ms"] / 1e3) * ws, "unit": UNIT,
                 "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
-        "split_precision" if args.precision == "fp64" else "fp64_path": {
+        "split_precision" if fp64 else "fp64_path": {
             "value": other_val, "unit": UNIT, "ms_per_step": other_r["ms"] / args.steps,
             "force_ms_per_launch": other_r["force_ms"],
-            "speedup_vs_fp64": (other_val / (value / ws)) if args.precision == "fp64" else None},
+            "speedup_vs_fp64": (other_val / (value / ws)) if fp64 else None,
+            "roofline": {"bound": "alu", "achieved": other_tf,
+                         "peak": FP32_PEAK_TF if fp64 else FP64_PEAK_TF, "unit": "TFLOP/s",
+                         "frac": other_tf / (FP32_PEAK_TF if fp64 else FP64_PEAK_TF),
+                         "traffic": cnt.get(other_k, {}).get("dram_bytes_per_launch"),
+                         "pipe_util_ncu": pipe_util(cnt.get(other_k), not fp64)}},
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

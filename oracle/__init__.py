@@ -115,6 +115,7 @@ def lib():
         L.orc_evaluate.argtypes = [C.c_void_p, C.c_int]
         L.orc_profile.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.orc_overflow.argtypes = [C.c_void_p]
+        L.orc_set_sample.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte)]
         _lib = L
     return _lib
 
@@ -327,6 +328,15 @@ class OracleSim:
         mu = np.zeros(1)
         lib().orc_profile(self._h, int(nbins), _dp(prof), _dp(mu))
         return prof, float(mu[0])
+
+    def set_sample(self, idx=None):
+        """Compute forces only for the particles in idx (None: all)."""
+        if idx is None:
+            lib().orc_set_sample(self._h, None)
+            return
+        mask = np.zeros(self.n, dtype=np.uint8)
+        mask[np.asarray(idx)] = 1
+        lib().orc_set_sample(self._h, mask.ctypes.data_as(C.POINTER(C.c_ubyte)))
 
     def overflow(self) -> bool:
         return bool(lib().orc_overflow(self._h))

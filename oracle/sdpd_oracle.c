@@ -80,6 +80,7 @@ typedef struct {
     int *new_n, *new_partner;
     double *new_delta;
     int overflow;
+    unsigned char *only;   /* if set: forces only for particles with only[i] != 0 */
 } orc_sim;
 
 /* ------------------------------------------------------------------ */
@@ -341,9 +342,22 @@ orc_sim *orc_create(const orc_params *P, int inst, int n, const double *x, const
     return s;
 }
 
+/* Restrict the force evaluation to the particles with mask[i] != 0 (a
+ * sample; every other stage still runs for all).  mask = NULL: all. */
+void orc_set_sample(orc_sim *s, const unsigned char *mask)
+{
+    free(s->only);
+    s->only = NULL;
+    if (mask) {
+        s->only = (unsigned char *)malloc((size_t)(s->n > 0 ? s->n : 1));
+        memcpy(s->only, mask, (size_t)s->n);
+    }
+}
+
 void orc_destroy(orc_sim *s)
 {
     if (!s) return;
+    free(s->only);
     void *ptrs[] = { s->x, s->v, s->w, s->type, s->R, s->m, s->I, s->lever, s->d, s->rho, s->p,
                      s->nb_off, s->nb, s->F_sdpd, s->F_pg, s->F_dg, s->F_rxn, s->F_dem, s->F_lub,
                      s->F_ext, s->F, s->N_sdpd, s->N_dem, s->N, s->vf, s->eps, s->Ssum,
@@ -666,6 +680,7 @@ static void compute_fluid(orc_sim *s)
 {
     const orc_params *P = &s->P;
     for (int i = 0; i < s->n; ++i) {
+        if (s->only && !s->only[i]) continue;
         double *Fs = s->F_sdpd + 3 * i, *Ns = s->N_sdpd + 3 * i, *Fp = s->F_pg + 3 * i;
         int ti = s->type[i];
         if (ti != T_FLUID && ti != T_RIGID) continue;
@@ -759,6 +774,7 @@ static void compute_fpi_reaction(orc_sim *s)
     const double h = P->r_c;
     for (int j = 0; j < s->n; ++j) {
         if (s->type[j] != T_FLUID) continue;
+        if (s->only && !s->only[j]) continue;
         for (int k = s->nb_off[j]; k < s->nb_off[j + 1]; ++k) {
             int i = s->nb[k];
             if (s->type[i] != T_RIGID || !(s->Ssum[i] > 0.0)) continue;
@@ -868,10 +884,16 @@ static void compute_rigid(orc_sim *s, int velver)
     int commit = (velver == 2);
     if (commit)
         for (int i = 0; i < s->n; ++i) s->new_n[i] = 0;
-    for (int i = 0; i < s->n; ++i) {
-        if (s->type[i] != T_RIGID) continue;
-        for (int j = 0; j < s->n; ++j) {
-            if (j == i || s->type[j] != T_RIGID) continue;
+    int nr = 0;
+    int *rig = (int *)malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(int));
+    for (int i = 0; i < s->n; ++i)
+        if (s->type[i] == T_RIGID) rig[nr++] = i;
+    for (int ri = 0; ri < nr; ++ri) {
+        const int i = rig[ri];
+        if (s->only && !s->only[i]) continue;
+        for (int rj = 0; rj < nr; ++rj) {
+            const int j = rig[rj];
+            if (j == i) continue;
             double r[3];
             double L = sqrt(pair_vec(P, s->x + 3 * i, s->x + 3 * j, r));
             double dsum = s->R[i] + s->R[j];
@@ -913,6 +935,7 @@ static void compute_rigid(orc_sim *s, int velver)
             }
         }
     }
+    free(rig);
     if (commit) {
         int *tn = s->hist_n; s->hist_n = s->new_n; s->new_n = tn;
         int *tp = s->hist_partner; s->hist_partner = s->new_partner; s->new_partner = tp;

@@ -458,12 +458,14 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     IALLOC(b.skey, N);
     IALLOC(b.nbflag, N);
     IALLOC(b.rev, (size_t)c->cap * c->Npad);
-    b.capown = c->cap;
+    // each particle owns about half of its list (hash ownership, spread of a
+    // few pairs): the pair buffer and the normals cache hold cap/2 + 64 rows
+    b.capown = std::min(c->cap, c->cap / 2 + 64);
     {
         const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
         char *pa = nullptr, *pb = nullptr, *oa = nullptr, *ob = nullptr;
-        IALLOC(pa, 4 * rs * (size_t)c->cap * c->Npad);
-        IALLOC(pb, 2 * rs * (size_t)c->cap * c->Npad);
+        IALLOC(pa, 4 * rs * (size_t)b.capown * c->Npad);
+        IALLOC(pb, 2 * rs * (size_t)b.capown * c->Npad);
         IALLOC(oa, 4 * rs * (size_t)N);
         IALLOC(ob, 2 * rs * (size_t)N);
         b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;
@@ -474,8 +476,8 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     {
         const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
         char *za = nullptr, *zb = nullptr;
-        IALLOC(za, 4 * rs * (size_t)c->cap * c->Npad);
-        IALLOC(zb, 2 * rs * (size_t)c->cap * c->Npad);
+        IALLOC(za, 4 * rs * (size_t)b.capown * c->Npad);
+        IALLOC(zb, 2 * rs * (size_t)b.capown * c->Npad);
         b.zA = za; b.zB = zb;
     }
     b.use_cache = 1;

@@ -273,7 +273,10 @@ __global__ void k_neighbors(Bufs b, const int *gate)
                 if (nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) W.put(entry, tj);
             }
         }
-        if (pass == 0) b.nfirst[s] = W.cnt < b.cap ? W.cnt : b.cap;
+        if (pass == 0) {
+            if (W.cnt > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+            b.nfirst[s] = min(W.cnt, min(b.cap, b.capown));
+        }
     }
     int cnt = W.cnt;
     if (cnt > b.cap) {
@@ -299,7 +302,7 @@ __global__ void k_rev(Bufs b, const int *gate)
     if (s >= b.N) return;
     const long long Np = b.Npad;
     const int first = b.nfirst[s], n = b.ncnt[s];
-    constexpr int G = 4;
+    constexpr int G = 4;  // (owned prefixes are <= capown, checked at the build)
     for (int k0 = first; k0 < n; k0 += G) {
         int part[G], lo[G], hi[G];
 #pragma unroll
