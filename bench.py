@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sedimentation", choices=sorted(WORKLOADS))
+    ap.add_argument("--paths", default="both", choices=["both", "main"],
+                    help="also time the other precision path (both) or not")
+    ap.add_argument("--max-neighbors", type=int, default=0)
     return ap.parse_args()
 
 
@@ -145,7 +148,7 @@ def time_native(args, ws, rank, local):
     prec = B.SDPD_PREC_FP64 if args.precision == "fp64" else B.SDPD_PREC_SPLIT
 
     def run_path(precision):
-        sim = B.Sim(case, precision=precision)
+        sim = B.Sim(case, precision=precision, max_neighbors=args.max_neighbors)
         sim.build_cells(stream)
         torch.cuda.synchronize()
         pairs = sim.count_pairs()
@@ -214,7 +217,9 @@ def time_native(args, ws, rank, local):
         return out
 
     main = run_path(prec)
-    other = run_path(B.SDPD_PREC_SPLIT if prec == B.SDPD_PREC_FP64 else B.SDPD_PREC_FP64)
+    other = None
+    if args.paths == "both":
+        other = run_path(B.SDPD_PREC_SPLIT if prec == B.SDPD_PREC_FP64 else B.SDPD_PREC_FP64)
     return main, other
 
 
@@ -326,7 +331,7 @@ def main():
     pairs = main_r["pairs"]
     value = pairs * 2 * args.steps * ws / (t_max / 1e3)
     steps_per_s = args.steps / (t_max / 1e3)
-    other_val = other_r["pairs"] * 2 * args.steps / (other_r["ms"] / 1e3)
+    other_val = other_r["pairs"] * 2 * args.steps / (other_r["ms"] / 1e3) if other_r else None
     peaks = measured_peaks()
     cnt = ncu_counters()
     fp64 = args.precision == "fp64"
@@ -334,7 +339,7 @@ def main():
     # sphere kernel), ALU bound; algorithmic flops = 160 per unordered pair
     force_flops = FLOPS_PER_PAIR * pairs
     achieved_tf = force_flops / (main_r["force_ms"] / 1e3) / 1e12
-    other_tf = FLOPS_PER_PAIR * other_r["pairs"] / (other_r["force_ms"] / 1e3) / 1e12
+    other_tf = FLOPS_PER_PAIR * other_r["pairs"] / (other_r["force_ms"] / 1e3) / 1e12 if other_r else None
     kd, kf = "k_force_half<double>", "k_force_half<float>"
     main_k, other_k = (kd, kf) if fp64 else (kf, kd)
     fp64_peak_tf = FP64_PEAK_TF if fp64 else FP32_PEAK_TF
@@ -362,7 +367,7 @@ def main():
                               "bytes of %s per launch (profiles/)") % ("FP64" if fp64 else "FP32", main_k)},
         "e2e": {"value": pairs * 2 / (main_r["e2e_ms"] / 1e3) * ws, "unit": UNIT,
                 "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
-        "split_precision" if fp64 else "fp64_path": {
+        "split_precision" if fp64 else "fp64_path": None if other_r is None else {
             "value": other_val, "unit": UNIT, "ms_per_step": other_r["ms"] / args.steps,
             "force_ms_per_launch": other_r["force_ms"],
             "speedup_vs_fp64": (other_val / (value / ws)) if fp64 else None,
@@ -373,7 +378,7 @@ def main():
                          "pipe_util_ncu": pipe_util(cnt.get(other_k), not fp64)}},
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "sedimentation":
         rec["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(rec))
