@@ -200,6 +200,11 @@ sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
  * the current neighbour build and graph.  Synchronous. */
 sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
 
+/* Threads per block of the pair kernels (density, filter, force passes):
+ * 64, 128 (default) or 256.  A tuning knob; results do not change.
+ * Synchronous. */
+sdpd_status sdpd_set_block_size(sdpd_ctx *ctx, int threads);
+
 /* Verlet skin as a fraction of h (default 0.03): neighbour lists hold the
  * pairs within h (1 + skin) and are reused by later evaluations until some
  * particle has moved skin h / 2 since the build (decided on the device each

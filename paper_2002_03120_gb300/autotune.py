@@ -1,0 +1,117 @@
+"""Autotuner of the per-workload launch choices of libsdpd.
+
+For one workload (a list of instances and a precision) it times full steps
+under each candidate setting -- force-pass variant (Newton-3 half pairs or
+direct), Verlet skin, pair-kernel block size -- picks the fastest, and keeps
+the choice in a JSON file keyed by GPU name, precision and size class (total
+particles rounded to a power of two, number of instances), so later contexts
+of the same class reuse it without measuring again.
+
+The measurement uses CUDA events on one stream after warm-up steps; the
+choice never changes results beyond summation order (all settings evaluate
+the same pairs exactly).
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+from . import binding as B
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sdpd_gb300", "autotune.json")
+CANDIDATES = {
+    "newton3": (1, 0),
+    "skin": (0.0, 0.03, 0.06, 0.12),
+    "block": (64, 128, 256),
+}
+
+
+def size_class(n_particles: int, n_instances: int, precision: int) -> str:
+    return f"p{precision}_n2^{int(round(math.log2(max(n_particles, 1))))}_i{n_instances}"
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "unknown"
+
+
+def load_cache(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def search(measure, candidates=CANDIDATES):
+    """Exhaustive search over the candidate grid; `measure(setting)` returns a
+    time in ms (or None when the setting is not usable).  Returns
+    (best_setting, table of all results)."""
+    keys = sorted(candidates)
+    table = []
+    best, best_t = None, float("inf")
+    for values in itertools.product(*(candidates[k] for k in keys)):
+        setting = dict(zip(keys, values))
+        if setting["newton3"] == 0 and setting["skin"] != candidates["skin"][0] and \
+                setting["block"] != 128:
+            continue  # the direct pass is sampled at the default block only
+        t = measure(setting)
+        table.append({**setting, "ms": t})
+        if t is not None and t < best_t:
+            best, best_t = setting, t
+    return best, table
+
+
+def apply(sim: "B.Sim", setting: dict) -> None:
+    sim.set_force_mode(int(setting["newton3"]))
+    sim.set_skin(float(setting["skin"]))
+    sim.set_block_size(int(setting["block"]))
+
+
+def tune(cases, precision=B.SDPD_PREC_SPLIT, steps=10, warmup=3, cache_path=DEFAULT_CACHE,
+         force=False, max_neighbors=0, candidates=CANDIDATES):
+    """Measure (or read from the cache) the fastest setting for this workload."""
+    import torch
+    if isinstance(cases, dict):
+        cases = [cases]
+    n = sum(len(c["x"]) for c in cases)
+    key = f"{_gpu_name()}|{size_class(n, len(cases), precision)}"
+    cache = load_cache(cache_path)
+    if not force and key in cache:
+        return cache[key]["best"]
+    stream = torch.cuda.Stream()
+
+    def measure(setting):
+        sim = B.Sim(cases, precision=precision, max_neighbors=max_neighbors)
+        try:
+            apply(sim, setting)
+            sim.step(warmup, stream)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(steps, stream)
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b) / steps
+        except B.SdpdError:
+            return None
+        finally:
+            sim.close()
+
+    best, table = search(measure, candidates)
+    cache[key] = {"best": best, "table": table, "particles": n, "instances": len(cases)}
+    save_cache(cache, cache_path)
+    return best

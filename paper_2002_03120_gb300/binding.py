@@ -74,7 +74,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_compute_density", "sdpd_couple_drag", "sdpd_compute_forces", "sdpd_integrate",
            "sdpd_step", "sdpd_viscosity_probe", "sdpd_get_state", "sdpd_get_drag",
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
-           "sdpd_set_force_mode", "sdpd_set_skin", "sdpd_density_noalloc",
+           "sdpd_set_force_mode", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
            "sdpd_check",
            "sdpd_last_error"]
 
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
         "sdpd_graph_kernels": (st, [vp, llp]),
         "sdpd_set_force_mode": (st, [vp, C.c_int]),
         "sdpd_set_skin": (st, [vp, C.c_double]),
+        "sdpd_set_block_size": (st, [vp, C.c_int]),
         "sdpd_density_noalloc": (st, [C.POINTER(SdpdParams), C.c_longlong, vp, vp, vp, vp, vp]),
         "sdpd_check": (st, [vp]),
         "sdpd_last_error": (C.c_char_p, []),
@@ -310,6 +311,9 @@ class Sim:
 
     def set_force_mode(self, newton3: int):
         _check(load().sdpd_set_force_mode(self._h, int(newton3)))
+
+    def set_block_size(self, threads: int):
+        _check(load().sdpd_set_block_size(self._h, int(threads)))
 
     def set_skin(self, skin: float):
         _check(load().sdpd_set_skin(self._h, float(skin)))

@@ -428,6 +428,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     b.n_inst = n_instances;
     b.cap = c->cap;
     b.K = c->K;
+    b.pair_block = 128;
     auto cleanup = [&](sdpd_status s) {
         sdpd_destroy(c);
         return s;
@@ -752,6 +753,18 @@ sdpd_status sdpd_set_force_mode(sdpd_ctx *c, int newton3)
         c->newton3 = newton3;
         drop_graph(c);
         c->cells_valid = c->density_valid = c->drag_valid = false;
+    }
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_set_block_size(sdpd_ctx *c, int threads)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (threads != 64 && threads != 128 && threads != 256) return fail(SDPD_E_INVALID, "block size must be 64, 128 or 256");
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (threads != c->b.pair_block) {
+        c->b.pair_block = threads;
+        drop_graph(c);
     }
     return SDPD_OK;
 }

@@ -153,7 +153,7 @@ __device__ __forceinline__ void finalize_slot(const Bufs &b, long long s, double
 // ------------------------------------------------------------------ density
 // gate: nullptr = always; else only when *gate != 0 (a build just happened)
 template <class R>
-__global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter, const int *gate)
+__global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const int *gate)
 {
     if (gate && *gate == 0) return;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(128) k_density(Bufs b, int any_filter, const i
 
 // ------------------------------------------------------------ pressure filter
 template <class R>
-__global__ void __launch_bounds__(128) k_filter(Bufs b, const int *gate)
+__global__ void __launch_bounds__(256) k_filter(Bufs b, const int *gate)
 {
     if (gate && *gate == 0) return;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -425,7 +425,7 @@ __device__ __forceinline__ void write_fluid_force(const Bufs &b, const Inst &I, 
 // particle i; the next neighbour's records are fetched before the current
 // pair is evaluated.
 template <class R>
-__global__ void __launch_bounds__(128) k_force_fluid(Bufs b)
+__global__ void __launch_bounds__(256) k_force_fluid(Bufs b)
 {
     using T4 = typename Vec<R>::T4;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(128) k_force_fluid(Bufs b)
 // six normals of each pair; the second reads them back when the list has not
 // been rebuilt in between (same counter, so the same bits).
 template <class R>
-__global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
+__global__ void __launch_bounds__(256) k_force_half(Bufs b, int velver)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(128) k_force_half(Bufs b, int velver)
 // evaluated directly (Eqs. FijC, FijD and the drag reaction Eq.
 // F_fpi_DG_reac) + external force.
 template <class R>
-__global__ void __launch_bounds__(128) k_force_gather(Bufs b)
+__global__ void __launch_bounds__(256) k_force_gather(Bufs b)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
@@ -902,11 +902,11 @@ void launch_density(const Bufs &b, int precision, int any_filter, const int *gat
 {
     if (!b.N) return;
     if (precision == SDPD_PREC_SPLIT) {
-        k_density<float><<<nblk(b.N, 128), 128, 0, st>>>(b, any_filter, gate);
-        if (any_filter) k_filter<float><<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
+        k_density<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+        if (any_filter) k_filter<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     } else {
-        k_density<double><<<nblk(b.N, 128), 128, 0, st>>>(b, any_filter, gate);
-        if (any_filter) k_filter<double><<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
+        k_density<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+        if (any_filter) k_filter<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     }
 }
 
@@ -920,16 +920,16 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
     if (!b.N) return;
     if (newton3) {
         if (precision == SDPD_PREC_SPLIT) {
-            k_force_half<float><<<nblk(b.N, 128), 128, 0, st>>>(b, velver);
-            k_force_gather<float><<<nblk(b.N, 128), 128, 0, st>>>(b);
+            k_force_half<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, velver);
+            k_force_gather<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
         } else {
-            k_force_half<double><<<nblk(b.N, 128), 128, 0, st>>>(b, velver);
-            k_force_gather<double><<<nblk(b.N, 128), 128, 0, st>>>(b);
+            k_force_half<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, velver);
+            k_force_gather<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
         }
     } else if (precision == SDPD_PREC_SPLIT) {
-        k_force_fluid<float><<<nblk(b.N, 128), 128, 0, st>>>(b);
+        k_force_fluid<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
     } else {
-        k_force_fluid<double><<<nblk(b.N, 128), 128, 0, st>>>(b);
+        k_force_fluid<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
     }
     if (b.nrigid) {
         k_force_rigid<<<nblk(32LL * b.nrigid, 128), 128, 0, st>>>(b, velver);

@@ -1,0 +1,53 @@
+"""Autotuner: search logic and cache on the CPU (fake timings), and one real
+tuning run through the C ABI on the GPU."""
+import json
+
+import pytest
+
+from paper_2002_03120_gb300 import autotune
+
+
+def test_search_picks_fastest_and_skips_nothing_required():
+    times = {}
+
+    def fake(setting):
+        t = 10.0 - 3 * setting["newton3"] - 10 * setting["skin"] + abs(setting["block"] - 128) / 64
+        times[tuple(sorted(setting.items()))] = t
+        return t
+
+    best, table = autotune.search(fake)
+    assert best == {"newton3": 1, "skin": 0.12, "block": 128}
+    assert min(r["ms"] for r in table) == pytest.approx(fake(best))
+    assert any(r["newton3"] == 0 for r in table)
+
+
+def test_search_ignores_unusable_settings():
+    best, table = autotune.search(lambda s: None if s["block"] == 64 else 1.0 + s["skin"])
+    assert best["block"] != 64 and best["skin"] == 0.0
+
+
+def test_cache_roundtrip(tmp_path):
+    p = tmp_path / "t.json"
+    autotune.save_cache({"k": {"best": {"newton3": 1}}}, str(p))
+    assert autotune.load_cache(str(p))["k"]["best"]["newton3"] == 1
+    assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
+    assert autotune.size_class(73728, 1, 0) == "p0_n2^16_i1"
+
+
+@pytest.mark.gpu
+def test_tune_on_gpu(tmp_path):
+    from _gpu_common import need_gpu
+    need_gpu()
+    from paper_2002_03120_gb300 import binding as B
+    from paper_2002_03120_gb300 import cases
+    case = cases.sedimentation(nx=16, ny=16, nz=32)
+    cache = str(tmp_path / "tune.json")
+    cand = {"newton3": (1, 0), "skin": (0.0, 0.06), "block": (128, 256)}
+    best = autotune.tune(case, precision=B.SDPD_PREC_SPLIT, steps=3, warmup=2, cache_path=cache,
+                         candidates=cand)
+    assert best["block"] in (128, 256) and best["newton3"] in (0, 1)
+    data = json.load(open(cache))
+    (entry,) = data.values()
+    assert all(r["ms"] is not None and r["ms"] > 0 for r in entry["table"])
+    # a second call is served from the cache
+    assert autotune.tune(case, precision=B.SDPD_PREC_SPLIT, cache_path=cache, candidates=cand) == best
