@@ -248,6 +248,41 @@ sdpd_status sdpd_density_noalloc(const sdpd_params *params, long long n, const d
 /* Wait for all work of the context and report a pending kernel error. */
 sdpd_status sdpd_check(sdpd_ctx *ctx);
 
+/* ---------------------------------------------------------------------------
+ * Apparent-viscosity surrogate (a build component; the paper has none): a
+ * multilayer perceptron 3 -> 128 -> 128 -> 128 -> 128 -> 1 with GELU (erf
+ * form), MSE loss and Adam (lr given, beta = (0.9, 0.999), eps = 1e-8).  The
+ * three 128 x 128 layers run on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation); the input/output layers and element-wise work in FP32.
+ * Parameters are one flat FP32 vector of mlp_param_count() values in the
+ * order W0 [128][3], b0 [128], W1 [128][128], b1, W2, b2, W3, b3, W4 [128],
+ * b4 [1] (W[out][in], row-major).  X is [n][3] FP32 (inputs scaled to about
+ * [0, 1] by the caller), targets and outputs [n] FP32, all in device memory.
+ * A network object is not thread-safe. */
+typedef struct sdpd_mlp sdpd_mlp;
+
+/* Create the network (in = 3, width = 128, depth = 4 are the only shape);
+ * He-uniform weights from `seed`, zero biases; training batches up to
+ * batch_max rows.  Synchronous. */
+sdpd_status mlp_init(int in, int width, int depth, unsigned long long seed, int batch_max, sdpd_mlp **out);
+void mlp_destroy(sdpd_mlp *net);
+int mlp_param_count(void);
+/* Replace the parameters (host or device pointer; resets Adam).  Synchronous. */
+sdpd_status mlp_set_params(sdpd_mlp *net, const float *params);
+/* Copy parameters and the last gradients out (NULL skips).  Synchronous. */
+sdpd_status mlp_get_params(sdpd_mlp *net, float *params, float *grads);
+/* Forward + backward of one batch without updating: gradients of the mean
+ * squared error; *loss (host, may be NULL) written after a synchronisation. */
+sdpd_status mlp_gradients(sdpd_mlp *net, const float *X, const float *T, int batch, float *loss, void *stream);
+/* One Adam step on one batch; *loss as for mlp_gradients. */
+sdpd_status mlp_train_step(sdpd_mlp *net, const float *X, const float *T, int batch, float lr, float *loss,
+                           void *stream);
+/* Predictions for n rows (persistent launch over 128-row tiles). */
+sdpd_status mlp_infer(sdpd_mlp *net, const float *X, float *Y, long long n, void *stream);
+/* Wait and report a pending error (a tensor-core completion wait that timed
+ * out is SDPD_E_TIMEOUT). */
+sdpd_status mlp_check(sdpd_mlp *net);
+
 /* Last error message of the calling thread (never NULL). */
 const char *sdpd_last_error(void);
 

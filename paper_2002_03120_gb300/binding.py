@@ -76,7 +76,8 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
            "sdpd_set_force_mode", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
            "sdpd_check",
-           "sdpd_last_error"]
+           "sdpd_last_error", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
+           "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
 
 
 def library_path() -> str:
@@ -125,6 +126,15 @@ def load(build_if_missing: bool = True):
         "sdpd_density_noalloc": (st, [C.POINTER(SdpdParams), C.c_longlong, vp, vp, vp, vp, vp]),
         "sdpd_check": (st, [vp]),
         "sdpd_last_error": (C.c_char_p, []),
+        "mlp_init": (st, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.POINTER(vp)]),
+        "mlp_destroy": (None, [vp]),
+        "mlp_param_count": (C.c_int, []),
+        "mlp_set_params": (st, [vp, vp]),
+        "mlp_get_params": (st, [vp, vp, vp]),
+        "mlp_gradients": (st, [vp, vp, vp, C.c_int, C.POINTER(C.c_float), vp]),
+        "mlp_train_step": (st, [vp, vp, vp, C.c_int, C.c_float, C.POINTER(C.c_float), vp]),
+        "mlp_infer": (st, [vp, vp, vp, C.c_longlong, vp]),
+        "mlp_check": (st, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -325,3 +335,57 @@ class Sim:
 
     def check(self):
         _check(load().sdpd_check(self._h))
+
+
+class Mlp:
+    """The tensor-core surrogate network (mlp_* entry points)."""
+
+    def __init__(self, seed: int = 0, batch_max: int = 256):
+        h = C.c_void_p()
+        _check(load().mlp_init(3, 128, 4, int(seed), int(batch_max), C.byref(h)))
+        self._h = h
+        self.n_params = int(load().mlp_param_count())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.n_params
+        _check(load().mlp_set_params(self._h, C.c_void_p(a.ctypes.data)))
+
+    def params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().mlp_get_params(self._h, C.c_void_p(p.ctypes.data), None))
+        return p
+
+    def grads(self):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().mlp_get_params(self._h, None, C.c_void_p(g.ctypes.data)))
+        return g
+
+    def gradients(self, X, T, stream=None) -> float:
+        loss = C.c_float()
+        _check(load().mlp_gradients(self._h, _ptr(X), _ptr(T), int(X.shape[0]), C.byref(loss),
+                                    _stream(stream)))
+        return loss.value
+
+    def train_step(self, X, T, lr=1e-3, stream=None, want_loss=True):
+        loss = C.c_float()
+        _check(load().mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),
+                                     C.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
+
+    def infer(self, X, Y, stream=None):
+        _check(load().mlp_infer(self._h, _ptr(X), _ptr(Y), int(X.shape[0]), _stream(stream)))
+
+    def check(self):
+        _check(load().mlp_check(self._h))

@@ -14,12 +14,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared(header):
     src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sdpd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b((?:sdpd|mlp)_[a-z_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
     names = _declared("sdpd.h")
-    for must in ("sdpd_init", "sdpd_build_cells", "sdpd_compute_forces", "sdpd_couple_drag",
+    for must in ("sdpd_init", "sdpd_build_cells", "sdpd_compute_forces", "sdpd_couple_drag", "mlp_train_step", "mlp_infer",
                  "sdpd_integrate", "sdpd_viscosity_probe"):
         assert must in names
 
