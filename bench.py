@@ -41,6 +41,8 @@ WORKLOADS = {
     "poiseuille": "reverse-Poiseuille 16x32x16 (8,192 fluid), fully periodic",
     "dambreak": "dam break 126x63x63 column (490,094 fluid + 10,000 spheres + 501,903 wall)",
     "batch": "batched viscometer sweep: 64 slurry instances, N_f log-uniform 20k-400k",
+    "surrogate": "apparent-viscosity MLP 3-128-128-128-128-1 (GELU, BF16 tensor cores): "
+                 "1e6-query inference; training epoch of 2,000 samples, batch 256",
 }
 # algorithmic flops of one evaluation of one unordered pair by the force pass
 # (Eqs. FijC, FijD, FijR, FijT incl. Box-Muller; transcendentals counted as 1)
@@ -223,6 +225,103 @@ def time_native(args, ws, rank, local):
     return main, other
 
 
+def time_surrogate(args, ws, rank, local):
+    """The surrogate network: one step = one 10^6-query inference launch
+    (inputs in HBM, L2 flushed before each); training throughput measured
+    beside it on 2,000 Sobol samples with a smooth synthetic target."""
+    import torch
+    from paper_2002_03120_gb300 import binding as B
+    from paper_2002_03120_gb300 import surrogate as S
+    from paper_2002_03120_gb300.sobol import sobol
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    nq = 1_000_000
+    g = torch.Generator(device="cpu").manual_seed(5 + rank)
+    Xh = torch.rand(nq, 3, generator=g).pin_memory()
+    X = Xh.to(dev)
+    Y = torch.empty(nq, dtype=torch.float32, device=dev)
+    Yh = torch.empty(nq, dtype=torch.float32).pin_memory()
+    net = B.Mlp(seed=11, batch_max=256)
+    U = sobol(2000, 3, skip=1).astype(np.float32)
+    T = (np.sin(3 * U[:, 0]) + U[:, 1] * U[:, 2] - 0.5 * U[:, 2] ** 2).astype(np.float32)
+    Ud, Td = torch.as_tensor(U, device=dev), torch.as_tensor(T, device=dev)
+    torch.cuda.synchronize()
+
+    def epoch():
+        for b0 in range(0, 2000, 256):
+            net.train_step(Ud[b0:b0 + 256], Td[b0:b0 + 256], lr=1e-3, stream=stream, want_loss=False)
+
+    for _ in range(args.warmup):
+        epoch()
+        net.infer(X, Y, stream)
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.infer(X, Y, stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    tr = []
+    for _ in range(max(3, args.steps // 4)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        epoch()
+        b.record(stream)
+        b.synchronize()
+        tr.append(a.elapsed_time(b))
+    e2e = []
+    for _ in range(max(3, args.steps // 2)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            X.copy_(Xh, non_blocking=True)
+            net.infer(X, Y, stream)
+            Yh.copy_(Y, non_blocking=True)
+            b.record(stream)
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    net.check()
+    t_ms = max_over_ranks(float(sum(ms)), ws)
+    per = t_ms / args.steps
+    fq = S.flops_per_query()
+    achieved = nq * fq / (per / 1e3) / 1e12
+    peak = measured_peaks().get("bf16_tflops") or 1900.0
+    cnt = {}
+    try:
+        cnt = json.load(open(os.path.join(ROOT, "profiles", "counters_surrogate.json")))
+    except Exception:
+        pass
+    rec = {
+        "metric": "surrogate inference queries/s", "value": nq * args.steps * ws / (t_ms / 1e3),
+        "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 GEMM operands / f32 accumulate", "data": "synthetic",
+        "config": {"workload": WORKLOADS["surrogate"], "queries_per_step": nq,
+                   "l2": "flushed (256 MB write) before every timed launch",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "roofline": {"kernel": "k_mlp_forward", "bound": "tensor", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": cnt.get("k_mlp_forward", {}).get("dram_bytes_per_launch"),
+                     "flop_per_query": fq,
+                     "note": "peak = measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
+        "e2e": {"value": nq / (float(np.mean(e2e)) / 1e3), "unit": "queries/s",
+                "h2d_bytes_per_step": nq * 12, "d2h_bytes_per_step": nq * 4},
+        "training": {"samples_per_s": 2000 / (float(np.median(tr)) / 1e3), "epoch_ms": float(np.median(tr)),
+                     "adam_steps_per_epoch": 8, "batch": 256},
+    }
+    if rank == 0:
+        print(json.dumps(rec))
+
+
 def max_over_ranks(v, ws):
     if ws == 1:
         return v
@@ -326,6 +425,12 @@ def main():
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
+    if args.workload == "surrogate":
+        time_surrogate(args, ws, rank, local)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     main_r, other_r = time_native(args, ws, rank, local)
     t_max = max_over_ranks(main_r["ms"], ws)
     pairs = main_r["pairs"]

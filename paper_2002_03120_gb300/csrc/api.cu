@@ -365,7 +365,7 @@ sdpd_status check_err(sdpd_ctx *c)
     if (e & ERR_PAIR_CAP) return fail(SDPD_E_CAPACITY, "pair buffer capacity exceeded");
     if (e & ERR_REV) return fail(SDPD_E_STATE, "neighbour lists not symmetric");
     if (e & ERR_NONFINITE) return fail(SDPD_E_NONFINITE, "non-finite position, velocity or spin");
-    if (e & ERR_DOMAIN) return fail(SDPD_E_DOMAIN, "particle outside the grid on a wall axis");
+    if (e & ERR_DOMAIN) return fail(SDPD_E_DOMAIN, "particle outside the grid (crossed a wall axis, or moved more than a box length in one step)");
     return fail(SDPD_E_CUDA, "unknown device error");
 }
 

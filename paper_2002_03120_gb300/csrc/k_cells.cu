@@ -22,9 +22,11 @@ namespace sdpd {
 #define GATE                                                                                    \
     if (gate && *gate == 0) return;
 
-__device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc, bool &out)
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc, bool &out, bool &nonfinite)
 {
-    int k = (int)floor((x - lo) * inv_cs);
+    const double f = floor((x - lo) * inv_cs);
+    nonfinite = !(fabs(f) < 1e9);   // NaN or a runaway coordinate
+    const int k = nonfinite ? 0 : (int)f;
     out = (k < 0) || (k >= nc);
     return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
 }
@@ -43,14 +45,16 @@ __global__ void k_cell_keys(Bufs b, const int *gate)
     if (g >= b.N) return;
     const Inst &I = b.inst[b.pinst[g]];
     int c[3];
-    bool bad = false;
+    bool bad = false, nf = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        bool o;
-        c[a] = cell_coord(b.x[3 * g + a], I.lo[a], I.inv_cs[a], I.nc[a], o);
+        bool o, f;
+        c[a] = cell_coord(b.x[3 * g + a], I.lo[a], I.inv_cs[a], I.nc[a], o, f);
         bad |= o;
+        nf |= f;
     }
-    if (bad) atomicOr(b.err, ERR_DOMAIN);
+    if (nf) atomicOr(b.err, ERR_NONFINITE);
+    else if (bad) atomicOr(b.err, ERR_DOMAIN);
     const int lin = (c[2] * I.nc[1] + c[1]) * I.nc[0] + c[0];
     const int key = I.cell_base + b.cell_rank[I.cell_base + lin];
     b.key[g] = key;
@@ -169,8 +173,8 @@ __global__ void k_gather(Bufs b, int precision, const int *gate)
         const double xs[3] = { x0, x1, x2 };
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            bool o;
-            c[a] = cell_coord(xs[a], I.lo[a], I.inv_cs[a], I.nc[a], o);
+            bool o, f;
+            c[a] = cell_coord(xs[a], I.lo[a], I.inv_cs[a], I.nc[a], o, f);
             xl[a] = xs[a] - (I.lo[a] + (double)c[a] * I.cs[a]);
         }
         b.A32[s] = make_float4((float)xl[0], (float)xl[1], (float)xl[2],

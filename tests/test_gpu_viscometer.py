@@ -23,7 +23,9 @@ def _gpu():
 def _meso(eta=25.0, seed=1, amp=1.5):
     c = cases.poiseuille_meso(nx=12, ny=24, nz=12, kBT=1e-3, eta=eta, amp=amp, seed=seed)
     p = c["params"]
-    p["dt"] = 0.1 * p["r_c"] / math.sqrt(p["alpha"] * p["p0"] / p["rho0"])
+    # acoustic limit, and the explicit friction limit of the dissipative pair
+    # force (about 0.3 / eta at rho0 = 3, r_c = 3.9 dx)
+    p["dt"] = min(0.1 * p["r_c"] / math.sqrt(p["alpha"] * p["p0"] / p["rho0"]), 0.3 / p["eta"])
     return c
 
 
