@@ -245,6 +245,16 @@ sdpd_status sdpd_graph_kernels(sdpd_ctx *ctx, long long *n_kernels);
 sdpd_status sdpd_density_noalloc(const sdpd_params *params, long long n, const double *x,
                                  const int *type, double *d_out, double *p_out, void *stream);
 
+/* The six standard normals z0..z5 of the random term of Eq. FijT for n
+ * pairs (gi[k], gj[k]) at `step`, exactly as the pair kernels draw them:
+ * Philox4x32-10 (Salmon et al., SC'11) keyed (seed low word, seed high word
+ * XOR inst), counter (min gid, max gid, step, block 0/1), uniforms
+ * ((u >> 9) + 1/2) 2^-23, Box-Muller in the given precision (SDPD_PREC_FP64
+ * or SDPD_PREC_SPLIT, FP32).  gi, gj: host [n]; z_out: host [n][6] doubles.
+ * Synchronous; needs no context.  Symmetric in (gi, gj). */
+sdpd_status sdpd_noise_normals(int precision, unsigned long long seed, int inst, unsigned step, long long n,
+                               const unsigned *gi, const unsigned *gj, double *z_out);
+
 /* Wait for all work of the context and report a pending kernel error. */
 sdpd_status sdpd_check(sdpd_ctx *ctx);
 

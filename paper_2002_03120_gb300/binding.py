@@ -76,7 +76,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
            "sdpd_set_force_mode", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
            "sdpd_check",
-           "sdpd_last_error", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
+           "sdpd_last_error", "sdpd_noise_normals", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
            "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
 
 
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True):
         "sdpd_density_noalloc": (st, [C.POINTER(SdpdParams), C.c_longlong, vp, vp, vp, vp, vp]),
         "sdpd_check": (st, [vp]),
         "sdpd_last_error": (C.c_char_p, []),
+        "sdpd_noise_normals": (st, [C.c_int, C.c_ulonglong, C.c_int, C.c_uint, C.c_longlong, vp, vp, vp]),
         "mlp_init": (st, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.POINTER(vp)]),
         "mlp_destroy": (None, [vp]),
         "mlp_param_count": (C.c_int, []),
@@ -335,6 +336,17 @@ class Sim:
 
     def check(self):
         _check(load().sdpd_check(self._h))
+
+
+def noise_normals(precision: int, seed: int, inst: int, step: int, gi, gj) -> np.ndarray:
+    """The six normals of the random pair term for pairs (gi, gj) ([n][6])."""
+    gi = np.ascontiguousarray(gi, dtype=np.uint32)
+    gj = np.ascontiguousarray(gj, dtype=np.uint32)
+    z = np.zeros((len(gi), 6))
+    _check(load().sdpd_noise_normals(int(precision), int(seed), int(inst), int(step), len(gi),
+                                     C.c_void_p(gi.ctypes.data), C.c_void_p(gj.ctypes.data),
+                                     C.c_void_p(z.ctypes.data)))
+    return z
 
 
 class Mlp:

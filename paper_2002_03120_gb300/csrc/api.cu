@@ -936,6 +936,35 @@ sdpd_status sdpd_count_pairs(sdpd_ctx *c, long long *n_pairs)
     return check_err(c);
 }
 
+sdpd_status sdpd_noise_normals(int precision, unsigned long long seed, int inst, unsigned step, long long n,
+                               const unsigned *gi, const unsigned *gj, double *z_out)
+{
+    if (n < 0 || (n && (!gi || !gj || !z_out)) || inst < 0 ||
+        (precision != SDPD_PREC_FP64 && precision != SDPD_PREC_SPLIT))
+        return fail(SDPD_E_INVALID, "sdpd_noise_normals: bad argument");
+    if (!n) return SDPD_OK;
+    (void)cudaGetLastError();
+    uint32_t *dg = nullptr;
+    double *dz = nullptr;
+    if (cudaMalloc(&dg, 2 * n * sizeof(uint32_t)) != cudaSuccess || cudaMalloc(&dz, 6 * n * sizeof(double)) != cudaSuccess) {
+        cudaFree(dg);
+        return fail(SDPD_E_OOM, "sdpd_noise_normals: cudaMalloc");
+    }
+    sdpd_status s = SDPD_OK;
+    if (cudaMemcpy(dg, gi, n * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dg + n, gj, n * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = fail(SDPD_E_CUDA, "sdpd_noise_normals: copy in");
+    if (s == SDPD_OK) {
+        const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32) ^ (uint32_t)inst;
+        launch_noise_normals(precision, n, dg, dg + n, step, k0, k1, dz, 0);
+        if (cudaMemcpy(z_out, dz, 6 * n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            s = fail(SDPD_E_CUDA, "sdpd_noise_normals: kernel or copy out");
+    }
+    cudaFree(dg);
+    cudaFree(dz);
+    return s;
+}
+
 sdpd_status sdpd_diagnostics(sdpd_ctx *c, int inst, double out[16])
 {
     if (!c || inst < 0 || inst >= c->n_inst || !out) return fail(SDPD_E_INVALID, "bad argument");

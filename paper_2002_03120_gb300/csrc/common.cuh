@@ -154,15 +154,64 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // Six standard normals of the pair {gi, gj} at `step`: two Philox blocks,
 // uniforms ((u >> 9) + 1/2) 2^-23 (exact in float and double), Box-Muller on
 // (u0,u1), (u2,u3), (u4,u5) in precision R.  Scalars only (no local arrays).
+// Table-driven FP64 pieces of the Box-Muller transform.  A uniform is
+// U = ((u >> 9) + 1/2) 2^-23 = w 2^-24 with w = 2 (u >> 9) + 1 odd and below
+// 2^24, so both the logarithm and the angle are taken from the integer w:
+//  * ln U (Tang's table-driven logarithm, ACM TOMS 16, 1990): w = 2^e f,
+//    f in [1, 2); c = 1 + j/128 from the top seven bits of f; f - c exact;
+//    ln U = (e - 24) ln 2 + ln c + log1p((f - c)/c), the series to r^7
+//    (r < 2^-7, truncation below 2^-59);
+//  * sin, cos of 2 pi w 2^-24: quadrant from the top two bits of w, the
+//    remaining angle split as (pi/2)(h/256) + t, h the next eight bits and
+//    t < (pi/2)/256, Taylor series of sin t (to t^5) and cos t (to t^6), and
+//    the angle-addition formulas.
+// Both are accurate to a few units in the last place.
+#include "bm_tables.cuh"
+
+__device__ __forceinline__ double bm_log_w(uint32_t w)
+{
+    const int e = 31 - __clz(w);
+    const uint64_t frac = e ? ((uint64_t)(w ^ (1u << e))) << (52 - e) : 0ull;
+    const int j = (int)(frac >> 45);
+    const double f = __longlong_as_double((long long)(0x3FF0000000000000ull | frac));
+    const double c = __longlong_as_double((long long)(0x3FF0000000000000ull | ((uint64_t)j << 45)));
+    const double2 t = __ldg(&BM_LOG_TAB[j]);
+    const double r = (f - c) * t.y;
+    double p = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    p = fma(p, r, 1.0 / 5.0);
+    p = fma(p, r, -0.25);
+    p = fma(p, r, 1.0 / 3.0);
+    p = fma(p, r, -0.5);
+    p = fma(p, r, 1.0);
+    return (__ldg(&BM_LOG_E[e]) + t.x) + p * r;
+}
+
+__device__ __forceinline__ void bm_sincos_w(uint32_t w, double &s, double &c)
+{
+    const uint32_t q = w >> 22, h = (w >> 14) & 255u, lo = w & 16383u;
+    const double lod = __longlong_as_double((long long)(0x4330000000000000ull | lo)) - 4503599627370496.0;
+    const double t = lod * (1.5707963267948966 / 4194304.0);
+    const double t2 = t * t;
+    const double sl = t * fma(t2, fma(t2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+    const double cl = fma(t2, fma(t2, fma(t2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    const double2 sc = __ldg(&BM_SC_TAB[h]);
+    const double sa = fma(sc.x, cl, sc.y * sl);
+    const double ca = fma(sc.y, cl, -(sc.x * sl));
+    s = (q & 1) ? ca : sa;
+    c = (q & 1) ? -sa : ca;
+    if (q & 2) {
+        s = -s;
+        c = -c;
+    }
+}
+
 template <class R> struct BoxMuller;
 template <> struct BoxMuller<double> {
     __device__ __forceinline__ static void pair(uint32_t ua, uint32_t ub, double &z0, double &z1)
     {
-        const double U1 = ((double)(ua >> 9) + 0.5) * (1.0 / 8388608.0);
-        const double U2 = ((double)(ub >> 9) + 0.5) * (1.0 / 8388608.0);
-        const double rad = sqrt(-2.0 * log(U1));
+        const double rad = sqrt(-2.0 * bm_log_w(((ua >> 9) << 1) | 1u));
         double s, c;
-        sincospi(2.0 * U2, &s, &c);
+        bm_sincos_w(((ub >> 9) << 1) | 1u, s, c);
         z0 = rad * c;
         z1 = rad * s;
     }
@@ -286,5 +335,7 @@ void launch_step_done(const Bufs &b, cudaStream_t st);
 void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long n);
 void launch_diag(const Bufs &b, int inst, cudaStream_t st, long long n);
 void launch_count_pairs(const Bufs &b, cudaStream_t st);
+void launch_noise_normals(int precision, long long n, const uint32_t *gi, const uint32_t *gj, uint32_t step,
+                          uint32_t k0, uint32_t k1, double *out, cudaStream_t st);
 
 }  // namespace sdpd

@@ -313,6 +313,30 @@ void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st)
     if (b.N) k_mark_pairs<<<nblk(b.N, 128), 128, 0, st>>>(b, flags);
 }
 
+// The six normals of the random term (Eq. FijT) of given pairs, as the pair
+// kernels draw them.
+template <class R>
+__global__ void k_noise_normals(long long n, const uint32_t *gi, const uint32_t *gj, uint32_t step, uint32_t k0,
+                                uint32_t k1, double *out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    R z[6];
+    pair_normals<R>(gi[i], gj[i], step, k0, k1, z[0], z[1], z[2], z[3], z[4], z[5]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[6 * i + k] = (double)z[k];
+}
+
+void launch_noise_normals(int precision, long long n, const uint32_t *gi, const uint32_t *gj, uint32_t step,
+                          uint32_t k0, uint32_t k1, double *out, cudaStream_t st)
+{
+    if (!n) return;
+    if (precision == SDPD_PREC_FP64)
+        k_noise_normals<double><<<nblk(n, 256), 256, 0, st>>>(n, gi, gj, step, k0, k1, out);
+    else
+        k_noise_normals<float><<<nblk(n, 256), 256, 0, st>>>(n, gi, gj, step, k0, k1, out);
+}
+
 void launch_count_pairs(const Bufs &b, cudaStream_t st)
 {
     cudaMemsetAsync(b.pair_count, 0, sizeof(unsigned long long), st);

@@ -131,10 +131,36 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// exp2 on the special-function unit (relative error about 2^-22)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula
+// 7.1.26 (Hastings' rational approximation), |error| <= 1.5e-7: one
+// reciprocal, one exponential, no branch.
+__device__ __forceinline__ float erf_as(float x)
+{
+    const float a = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, a, 1.0f));
+    float p = fmaf(1.061405429f, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    p *= t;
+    const float r = fmaf(-p, ex2_approx(-a * a * 1.44269504088896341f), 1.0f);
+    return copysignf(r, x);
+}
+
+// GELU, erf form: 0.5 z (1 + erf(z / sqrt 2)), and its derivative
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_prime(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) +
+           z * ex2_approx(-0.5f * 1.44269504088896341f * z * z) * 0.39894228040143268f;
 }
 
 // Eight values of one row, written as one 16-byte core-matrix row.
@@ -224,60 +250,130 @@ __device__ void stage_weights(uint8_t *tile, const __nv_bfloat16 *W, bool transp
 }
 
 // ------------------------------------------------------------- inference
-// Persistent over 128-row tiles; the three hidden weight tiles stay in
-// shared memory for the whole launch.
-__global__ void __launch_bounds__(128, 1) k_mlp_forward(const float *__restrict__ P,
-                                                        const __nv_bfloat16 *__restrict__ Wb,
-                                                        const float *__restrict__ X, float *__restrict__ Y,
-                                                        long long n, int *err)
+// Persistent over 128-row tiles with NWG warpgroups per CTA: each warpgroup
+// owns one tile at a time (its own activation operand in shared memory and
+// its own 128 accumulator columns in tensor memory) and synchronises only
+// with itself (named barrier g + 1), so the MMAs of one warpgroup overlap
+// the GELU epilogues of the others.  The three hidden weight tiles are
+// staged once per CTA and shared.
+constexpr int NWG = 4;
+constexpr size_t FWD_SMEM = (size_t)(3 + NWG) * TILE_BYTES + 128;
+
+__device__ __forceinline__ void wg_bar(int g) { asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory"); }
+
+// Row r (output unit) of one hidden weight tile, as the B operand.
+__device__ __forceinline__ void stage_row(uint8_t *tile, const __nv_bfloat16 *W, int r)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(W + r * WID);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) *reinterpret_cast<uint4 *>(tile + core_off(r, 8 * c)) = __ldg(src + c);
+}
+
+// D(128 x 128) = A . B^T for warpgroup g; thread tt == 0 of the warpgroup
+// issues, all 128 threads wait.  A timeout in any thread is seen by all
+// (flag in shared memory read after the barrier), so the warpgroup leaves
+// its loop together.
+__device__ bool wg_gemm(uint8_t *A, uint8_t *B, uint32_t dtmem, uint64_t *mbar, uint32_t &parity, int g,
+                        int tt, volatile int *flag, int *err)
+{
+    proxy_fence();
+    tc_fence_before();
+    wg_bar(g);
+    if (tt == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) mma_bf16(dtmem, make_desc(a0 + s * 256), make_desc(b0 + s * 256), s > 0 ? 1 : 0);
+        mma_commit(mbar);
+    }
+    if (!mbar_wait(mbar, parity)) {
+        *flag = 1;
+        atomicOr(err, ERR_MMA_TIMEOUT);
+        (void)mbar_wait(mbar, parity);
+    }
+    parity ^= 1u;
+    tc_fence_after();
+    wg_bar(g);
+    return *flag == 0;
+}
+
+__global__ void __launch_bounds__(128 * NWG, 1) k_mlp_forward(const float *__restrict__ P,
+                                                              const __nv_bfloat16 *__restrict__ Wb,
+                                                              const float *__restrict__ X, float *__restrict__ Y,
+                                                              long long n, int *err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *sB = smem;                      // 3 weight tiles
-    uint8_t *sA = smem + 3 * TILE_BYTES;     // activations
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 4 * TILE_BYTES);
-    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 4 * TILE_BYTES + 16);
-    const int t = threadIdx.x;
-    for (int l = 0; l < 3; ++l) stage_weights(sB + l * TILE_BYTES, Wb + l * WID * WID, false);
-    if (t == 0) mbar_init(mbar);
-    if (t < 32) tc_alloc(slot, 128);
+    uint8_t *sB = smem;                                        // 3 weight tiles
+    const int g = threadIdx.x >> 7, tt = threadIdx.x & 127;
+    uint8_t *sA = smem + (3 + g) * TILE_BYTES;                 // this warpgroup's activations
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + (3 + NWG) * TILE_BYTES) + g;
+    volatile int *flag = reinterpret_cast<int *>(smem + (3 + NWG) * TILE_BYTES + 64) + g;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + (3 + NWG) * TILE_BYTES + 96);
+    for (int r = threadIdx.x; r < 3 * WID; r += blockDim.x)
+        stage_row(sB + (r >> 7) * TILE_BYTES, Wb + (r >> 7) * WID * WID, r & 127);
+    if (tt == 0) {
+        mbar_init(mbar);
+        *flag = 0;
+    }
+    if (threadIdx.x < 32) tc_alloc(slot, 128 * NWG);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t taddr = *slot;
+    const uint32_t tcols = *slot + (uint32_t)(g * WID);                         // this warpgroup's columns
+    const uint32_t tl = tcols + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16);  // + this warp's lanes
+    const float4 *P4 = reinterpret_cast<const float4 *>(P);
     uint32_t parity = 0;
     bool ok = true;
-    for (long long tile = blockIdx.x; ok && tile * WID < n; tile += gridDim.x) {
-        const long long row = tile * WID + t;
+    for (long long tile = (long long)blockIdx.x * NWG + g; ok && tile * WID < n; tile += (long long)gridDim.x * NWG) {
+        const long long row = tile * WID + tt;
         const bool valid = row < n;
         const float x0 = valid ? X[3 * row] : 0.f, x1 = valid ? X[3 * row + 1] : 0.f,
                     x2 = valid ? X[3 * row + 2] : 0.f;
-        float v[16];
+        // input layer 3 -> 128 (FP32), W0 rows 8c..8c+7 = 24 floats = 6 float4
+#pragma unroll 2
         for (int c = 0; c < 16; ++c) {
-            float h[8];
+            float w[24], bb[8], h[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int o = 8 * c + i;
-                h[i] = gelu(P[OFF_W0 + 3 * o] * x0 + P[OFF_W0 + 3 * o + 1] * x1 + P[OFF_W0 + 3 * o + 2] * x2 +
-                            P[OFF_B0 + o]);
+            for (int k = 0; k < 6; ++k) {
+                const float4 q = __ldg(P4 + (OFF_W0 / 4) + 6 * c + k);
+                w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
             }
-            put8(sA, t, 8 * c, h);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float4 q = __ldg(P4 + (OFF_B0 / 4) + 2 * c + k);
+                bb[4 * k] = q.x; bb[4 * k + 1] = q.y; bb[4 * k + 2] = q.z; bb[4 * k + 3] = q.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) h[i] = gelu(fmaf(w[3 * i], x0, fmaf(w[3 * i + 1], x1, fmaf(w[3 * i + 2], x2, bb[i]))));
+            put8(sA, tt, 8 * c, h);
         }
         float y = 0.f;
-        for (int l = 1; l <= 3 && ok; ++l) {
-            ok = gemm_128(sA, sB + (l - 1) * TILE_BYTES, taddr, false, mbar, parity, err);
+        for (int l = 1; l <= 3; ++l) {
+            ok = wg_gemm(sA, sB + (l - 1) * TILE_BYTES, tcols, mbar, parity, g, tt, flag, err);
             if (!ok) break;
             for (int c = 0; c < 8; ++c) {
-                acc_row16(taddr, c, v);
+                float v[16];
+                tc_ld16(tl + (uint32_t)(c * 16), v);
+                float bb[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int o = 16 * c + i;
-                    const float h = gelu(v[i] + P[off_b(l) + o]);
-                    if (l < 3) v[i] = h;
-                    else y += h * P[OFF_W4 + o];
+                for (int k = 0; k < 4; ++k) {
+                    const float4 q = __ldg(P4 + off_b(l) / 4 + 4 * c + k);
+                    bb[4 * k] = q.x; bb[4 * k + 1] = q.y; bb[4 * k + 2] = q.z; bb[4 * k + 3] = q.w;
                 }
                 if (l < 3) {
-                    put8(sA, t, 16 * c, v);
-                    put8(sA, t, 16 * c + 8, v + 8);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + bb[i]);
+                    put8(sA, tt, 16 * c, v);
+                    put8(sA, tt, 16 * c + 8, v + 8);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float4 q = __ldg(P4 + OFF_W4 / 4 + 4 * c + k);
+                        y = fmaf(gelu(v[4 * k] + bb[4 * k]), q.x, y);
+                        y = fmaf(gelu(v[4 * k + 1] + bb[4 * k + 1]), q.y, y);
+                        y = fmaf(gelu(v[4 * k + 2] + bb[4 * k + 2]), q.z, y);
+                        y = fmaf(gelu(v[4 * k + 3] + bb[4 * k + 3]), q.w, y);
+                    }
                 }
             }
         }
@@ -285,7 +381,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward(const float *__restrict_
     }
     tc_fence_before();
     __syncthreads();
-    if (t < 32) tc_dealloc(taddr, 128);
+    if (threadIdx.x < 32) tc_dealloc(*slot, 128 * NWG);
 }
 
 // ------------------------------------------------------------- training
@@ -571,7 +667,7 @@ sdpd_status mlp_init(int in, int width, int depth, unsigned long long seed, int 
     cudaMemset(n.err, 0, 4);
     n.step = 0;
     k_mlp_refresh<<<(3 * WID * WID + 255) / 256, 256>>>(n);
-    cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FWD_SMEM);
     cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         mlp_destroy(h);
@@ -662,9 +758,9 @@ sdpd_status mlp_infer(sdpd_mlp *h, const float *X, float *Y, long long n, void *
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = (n + WID - 1) / WID;
-    const int grid = (int)std::min<long long>(tiles, (long long)nsm);
+    const int grid = (int)std::min<long long>((tiles + NWG - 1) / NWG, (long long)nsm);
     (void)cudaGetLastError();
-    k_mlp_forward<<<grid, 128, SMEM_BYTES, (cudaStream_t)stream>>>(h->net.P, h->net.Wb, X, Y, n, h->net.err);
+    k_mlp_forward<<<grid, 128 * NWG, FWD_SMEM, (cudaStream_t)stream>>>(h->net.P, h->net.Wb, X, Y, n, h->net.err);
     if (cudaGetLastError() != cudaSuccess) return mlp_fail(SDPD_E_CUDA, "mlp_infer: launch");
     return SDPD_OK;
 }

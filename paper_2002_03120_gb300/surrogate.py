@@ -18,10 +18,10 @@ not have:
 Instances are in the paper's mesoscale units (rho0 = 3, p0 = beta = 100,
 alpha = 7, r_c = 3.9 dx); the viscosity follows an Arrhenius law in T scaled to
 eta = 25 at 293.15 K, kBT = kbt_scale * T / 293.15, spheres of diameter 3 dx
-and density 2.7 rho0 on random lattice sites.  The forcing amplitude spans
-one decade, 0.3 to 3 (the paper's 1.5 lies inside): above it the peak velocity
-approaches the artificial sound speed, below it the thermal noise dominates
-the read-out.
+and density 2.7 rho0 on random lattice sites, lubrication gap floored at
+0.1 d.  The forcing amplitude spans one decade, 0.1 to 1: the peak velocity
+of the lowest viscosity stays below 0.2 of the artificial sound speed, and at
+the highest viscosity it stays above the thermal velocity sqrt(kBT/m).
 
 Run as a program it generates a data set, trains, times the inference and
 proposes points:  python -m paper_2002_03120_gb300.surrogate --runs 2000
@@ -41,7 +41,7 @@ from .sobol import sobol
 
 PHI = (0.0, 0.3)
 TEMP = (280.0, 350.0)
-AMP = (0.3, 3.0)
+AMP = (0.1, 1.0)
 ETA_REF = 25.0
 
 
@@ -69,19 +69,22 @@ def sweep_points(n: int, skip: int = 0) -> np.ndarray:
 
 def meso_dt(p) -> float:
     """Time step of a mesoscale instance: the acoustic limit 0.1 r_c / c and
-    the explicit limit of the dissipative pair friction.  The friction rate
-    of one particle is about sum_j gamma_a (1 + 1/3) x 2 over its ~250
-    neighbours, 3.7 eta at rho0 = 3 and r_c = 3.9 dx; velocity Verlet stays
-    stable while dt times that rate is below 2, so dt = 0.3 / eta keeps a
-    margin of about 1.8."""
+    the explicit limit of the velocity-proportional pair forces.  The
+    dissipative friction rate of one particle is about 3.7 eta at rho0 = 3
+    and r_c = 3.9 dx (sum over ~250 neighbours of gamma_a (1 + 1/3) x 2);
+    the drag and lubrication rates of a sphere (Ergun at eps ~ 0.5, gap at its
+    floor of 0.1 d, several partners) scale with eta as well.  Velocity
+    Verlet applied to a force -k v is stable for k dt < 4 and free of
+    overshoot for k dt < 2; dt = 0.2 / eta keeps the fluid at 0.74 and the
+    stiffest sphere configurations below 2."""
     c = math.sqrt(p["alpha"] * p["p0"] / p["rho0"])
-    return min(0.1 * p["r_c"] / c, 0.3 / p["eta"])
+    return min(0.1 * p["r_c"] / c, 0.2 / p["eta"])
 
 
 def instance(pt, seed: int, n: int = 12, kbt_scale: float = 0.01) -> dict:
     phi, T, g = (float(v) for v in pt)
     c = cases.viscometer_instance(2 * n ** 3, phi, T, g, seed=seed, mesoscale=True,
-                                  kBT=kbt_scale * T / 293.15)
+                                  kBT=kbt_scale * T / 293.15, lub_gap_min=0.1)
     p = c["params"]
     p["dt"] = meso_dt(p)
     return c
