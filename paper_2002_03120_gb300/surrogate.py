@@ -214,6 +214,10 @@ def main(argv=None):
     hok = np.isfinite(hmu)
     hm, _ = ens.predict(torch.as_tensor(features(hpts[hok]), device="cuda"))
     herr = np.abs(from_target(hm.cpu().numpy()) / hmu[hok] - 1.0)
+    # without the surrogate: the fluid viscosity law mu(T) (solids ignored)
+    eta_T = np.array([ETA_REF * cases.arrhenius_viscosity(T) / cases.arrhenius_viscosity(293.15)
+                      for T in hpts[hok][:, 1]])
+    lerr = np.abs(eta_T / hmu[hok] - 1.0)
     # 1e6-query inference, one network, CUDA events
     U = torch.rand(1_000_000, 3, device="cuda")
     Y = torch.empty(1_000_000, device="cuda")
@@ -232,6 +236,9 @@ def main(argv=None):
     rep = dict(runs=a.runs, valid=int(ok.sum()), data_s=t_data, train_s=t_train,
                train_mse=losses, heldout=int(hok.sum()),
                heldout_rel_err_median=float(np.median(herr)), heldout_rel_err_p90=float(np.quantile(herr, 0.9)),
+               fluid_law_rel_err_median=float(np.median(lerr)), fluid_law_rel_err_p90=float(np.quantile(lerr, 0.9)),
+               target_miss_median=float(np.nanmedian(np.abs(mu_t / a.target - 1.0))),
+               sobol_target_miss_median=float(np.nanmedian(np.abs(hmu[:len(mu_t)] / a.target - 1.0))),
                infer_1e6_ms=t_inf * 1e3, infer_tflops=1e6 * flops_per_query() / t_inf / 1e12,
                target=a.target, proposed=pt_t.tolist(), predicted=from_target(pred_t).tolist(),
                simulated=mu_t.tolist(),
