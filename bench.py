@@ -293,11 +293,7 @@ def time_surrogate(args, ws, rank, local):
     fq = S.flops_per_query()
     achieved = nq * fq / (per / 1e3) / 1e12
     peak = measured_peaks().get("bf16_tflops") or 1900.0
-    cnt = {}
-    try:
-        cnt = json.load(open(os.path.join(ROOT, "profiles", "counters_surrogate.json")))
-    except Exception:
-        pass
+    cnt = ncu_counters("counters_surrogate")
     rec = {
         "metric": "surrogate inference queries/s", "value": nq * args.steps * ws / (t_ms / 1e3),
         "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -312,6 +308,9 @@ def time_surrogate(args, ws, rank, local):
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": cnt.get("k_mlp_forward", {}).get("dram_bytes_per_launch"),
                      "flop_per_query": fq,
+                     "pipe_util_ncu": None if not cnt else {
+                         k: cnt["k_mlp_forward"][k + "_pct"] / 100.0
+                         for k in ("tensor_pipe", "fma_pipe", "alu_pipe", "issue_active")},
                      "note": "peak = measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
         "e2e": {"value": nq / (float(np.mean(e2e)) / 1e3), "unit": "queries/s",
                 "h2d_bytes_per_step": nq * 12, "d2h_bytes_per_step": nq * 4},
@@ -360,12 +359,12 @@ def _oracle_pairs(sim, case):
     return int(np.sum(mob[ij[:, 0]] | mob[ij[:, 1]]))
 
 
-def ncu_counters():
-    """ncu counters of the profiled force kernels (profiles/), used only while
-    the kernel source is the one that was profiled."""
+def ncu_counters(name="counters_sedimentation"):
+    """ncu counters of profiled kernels (profiles/<name>.json), used only
+    while the kernel source is the one that was profiled."""
     import hashlib
     try:
-        c = json.load(open(os.path.join(ROOT, "profiles", "counters_sedimentation.json")))
+        c = json.load(open(os.path.join(ROOT, "profiles", name + ".json")))
         src = open(os.path.join(ROOT, c["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != c["source_sha256_16"]:
             return {}
