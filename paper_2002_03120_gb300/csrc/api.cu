@@ -466,7 +466,8 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
         char *pa = nullptr, *pb = nullptr, *oa = nullptr, *ob = nullptr;
         IALLOC(pa, 4 * rs * (size_t)b.capown * c->Npad);
-        IALLOC(pb, 2 * rs * (size_t)b.capown * c->Npad);
+        // the split path keeps {o, ce} in resA only
+        IALLOC(pb, precision == SDPD_PREC_SPLIT ? 16 : 2 * rs * (size_t)b.capown * c->Npad);
         IALLOC(oa, 4 * rs * (size_t)N);
         IALLOC(ob, 2 * rs * (size_t)N);
         b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;

@@ -87,7 +87,8 @@ struct Bufs {
     uint16_t *rev;             // non-owned entry k of s -> position of s in the partner's list
     uint8_t *nbflag;           // per slot: bit 0 = has a rigid neighbour
     int capown;                // owned entries per particle in the pair buffer
-    void *resA, *resB;         // pair results [capown][Npad]: R4 {f, t.x}, R2 {t.y, t.z}
+    void *resA, *resB;         // pair results [capown][Npad]: FP64 R4 {f, h.x}, R2 {h.y, h.z}
+                               // (h = e x o); split float4 {o, ce}, resB unused
     void *ownA, *ownB;         // per slot sums of the owned pairs
     // fluid-particle interaction per rigid index
     double *eps, *fdg;         // eps [nr], drag [nr][3]

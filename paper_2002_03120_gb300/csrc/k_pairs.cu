@@ -357,6 +357,30 @@ template <class R> struct Z6 {
     R z0, z1, z2, z3, z4, z5;
 };
 
+// f = o + ce e and h = e x o of a pair in a fixed operation order, so that
+// the partner of the split path, which rebuilds them from {o, ce} and its
+// own (negated, bitwise equal) e, gets the owner's values exactly.
+__device__ __forceinline__ void pair_fh(float ox, float oy, float oz, float ce, float ex, float ey, float ez,
+                                        float &gx, float &gy, float &gz, float &hx, float &hy, float &hz)
+{
+    gx = __fmaf_rn(ce, ex, ox);
+    gy = __fmaf_rn(ce, ey, oy);
+    gz = __fmaf_rn(ce, ez, oz);
+    hx = __fmaf_rn(ey, oz, -__fmul_rn(ez, oy));
+    hy = __fmaf_rn(ez, ox, -__fmul_rn(ex, oz));
+    hz = __fmaf_rn(ex, oy, -__fmul_rn(ey, ox));
+}
+__device__ __forceinline__ void pair_fh(double ox, double oy, double oz, double ce, double ex, double ey, double ez,
+                                        double &gx, double &gy, double &gz, double &hx, double &hy, double &hz)
+{
+    gx = fma(ce, ex, ox);
+    gy = fma(ce, ey, oy);
+    gz = fma(ce, ez, oz);
+    hx = fma(ey, oz, -__dmul_rn(ez, oy));
+    hy = fma(ez, ox, -__dmul_rn(ex, oz));
+    hz = fma(ex, oy, -__dmul_rn(ey, ox));
+}
+
 // SDPD force on i from j (Eqs. FijC, FijD, FijR, FijT) for a pair already
 // known to lie within h, written as
 //   f = o + ce * e,   o = the part not along e_ij (v_ij, rotational, random),
@@ -563,14 +587,19 @@ __global__ void __launch_bounds__(256) k_force_half(Bufs b, int velver)
             zA[at] = za;
             zB[at] = zb;
         }
-        const R gx = ox + ce * ex, gy = oy + ce * ey, gz = oz + ce * ez;
-        const R hx = ey * oz - ez * oy, hy = ez * ox - ex * oz, hz = ex * oy - ey * ox;
+        R gx, gy, gz, hx, hy, hz;
+        pair_fh(ox, oy, oz, ce, ex, ey, ez, gx, gy, gz, hx, hy, hz);
         T4 ra;
-        ra.x = gx; ra.y = gy; ra.z = gz; ra.w = hx;
-        T2 rb;
-        rb.x = hy; rb.y = hz;
+        if constexpr (sizeof(R) == 4) {
+            // split path: {o, ce} (16 B); the partner rebuilds f and e x o
+            ra.x = ox; ra.y = oy; ra.z = oz; ra.w = ce;
+        } else {
+            ra.x = gx; ra.y = gy; ra.z = gz; ra.w = hx;
+            T2 rb;
+            rb.x = hy; rb.y = hz;
+            resB[at] = rb;
+        }
         resA[at] = ra;
-        resB[at] = rb;
         fx += gx; fy += gy; fz += gz;
         tx += hx; ty += hy; tz += hz;
     }
@@ -616,6 +645,7 @@ __global__ void __launch_bounds__(256) k_force_gather(Bufs b)
     constexpr int G = 4;
     for (int k0 = first; k0 < n; k0 += G) {
         long long at[G];
+        int pj[G];
         bool use[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -623,23 +653,48 @@ __global__ void __launch_bounds__(256) k_force_gather(Bufs b)
             use[g] = k < n;
             const int i = use[g] ? __ldg(nb + (long long)k * Np) : 0;
             if (use[g] && any_rigid) use[g] = mir_type(A[i]) != T_RIGID;
+            pj[g] = i;
             at[g] = use[g] ? (long long)__ldg(rv + (long long)k * Np) * Np + i : 0;
         }
         T4 ra[G];
-        T2 rb[G];
+        if constexpr (sizeof(R) == 4) {
+            T4 Ap[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            if (use[g]) {
-                ra[g] = resA[at[g]];
-                rb[g] = resB[at[g]];
+            for (int g = 0; g < G; ++g) {
+                if (use[g]) {
+                    ra[g] = resA[at[g]];
+                    Ap[g] = A[pj[g]];
+                }
             }
-        }
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            // NaN marks a pair beyond h (written by the owner)
-            if (!use[g] || isnan(ra[g].x)) continue;
-            fx -= ra[g].x; fy -= ra[g].y; fz -= ra[g].z;
-            tx += ra[g].w; ty += rb[g].x; tz += rb[g].y;
+            for (int g = 0; g < G; ++g) {
+                // NaN marks a pair beyond h (written by the owner)
+                if (!use[g] || isnan(ra[g].x)) continue;
+                // e of the owner = -(e seen from here), bitwise
+                R rx, ry, rz;
+                geo.disp(Ai, Ap[g], rx, ry, rz);
+                const R ir = rsqrt_<R>(rx * rx + ry * ry + rz * rz);
+                R gx, gy, gz, hx, hy, hz;
+                pair_fh(ra[g].x, ra[g].y, ra[g].z, ra[g].w, -(rx * ir), -(ry * ir), -(rz * ir), gx, gy, gz,
+                        hx, hy, hz);
+                fx -= gx; fy -= gy; fz -= gz;
+                tx += hx; ty += hy; tz += hz;
+            }
+        } else {
+            T2 rb[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (use[g]) {
+                    ra[g] = resA[at[g]];
+                    rb[g] = resB[at[g]];
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (!use[g] || isnan(ra[g].x)) continue;
+                fx -= ra[g].x; fy -= ra[g].y; fz -= ra[g].z;
+                tx += ra[g].w; ty += rb[g].x; tz += rb[g].y;
+            }
         }
     }
     const R lev = K<R>::lever(I);

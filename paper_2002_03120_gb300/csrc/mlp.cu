@@ -155,8 +155,27 @@ __device__ __forceinline__ float erf_as(float x)
     return copysignf(r, x);
 }
 
-// GELU, erf form: 0.5 z (1 + erf(z / sqrt 2)), and its derivative
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// GELU, erf form: 0.5 z (1 + erf(z / sqrt 2)) = z (1 - h) for z >= 0 and
+// z h for z < 0, with h = 0.5 erfc(|z| / sqrt 2) = 0.5 P(t) exp(-z^2 / 2) from
+// the same Abramowitz & Stegun 7.1.26 polynomial (coefficients halved).
+__device__ __forceinline__ float gelu(float z)
+{
+    const float a = fabsf(z) * 0.70710678118654752f;
+    const float t = rcp_approx(fmaf(0.3275911f, a, 1.0f));
+    float p = fmaf(0.5f * 1.061405429f, t, 0.5f * -1.453152027f);
+    p = fmaf(p, t, 0.5f * 1.421413741f);
+    p = fmaf(p, t, 0.5f * -0.284496736f);
+    p = fmaf(p, t, 0.5f * 0.254829592f);
+    const float h = (p * t) * ex2_approx(z * z * -0.72134752044448170f);
+    return z * (z >= 0.0f ? 1.0f - h : h);
+}
 __device__ __forceinline__ float gelu_prime(float z)
 {
     return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) +
