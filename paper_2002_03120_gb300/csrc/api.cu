@@ -473,6 +473,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;
     }
     IALLOC(b.xl64, N); IALLOC(b.dsp, N);
+    IALLOC(b.aclose, N); IALLOC(b.aclose_ok, 1);
     IALLOC(b.need_build, 1); IALLOC(b.fresh, 1);
     IALLOC(b.list_epoch, 1); IALLOC(b.cache_epoch, 1); IALLOC(b.cache_step, 1);
     {
@@ -487,6 +488,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     IALLOC(b.probe, 4096 * 2 + 64);
 #undef IALLOC
     if (cudaMemset(b.need_build, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.fresh, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(b.aclose_ok, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b.list_epoch, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(b.cache_epoch, 0xFF, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(b.cache_step, 0xFF, sizeof(long long)) != cudaSuccess)

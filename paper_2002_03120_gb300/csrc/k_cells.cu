@@ -350,6 +350,7 @@ __global__ void k_build_done(Bufs b, const int *gate)
     *b.list_epoch += 1u;
     *b.need_build = 0;
     *b.fresh = 1;
+    *b.aclose_ok = 0;   // slots were reassigned
 }
 
 // ---------------------------------------------------------------- launchers

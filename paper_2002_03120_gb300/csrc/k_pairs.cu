@@ -157,10 +157,16 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
 {
     if (gate && *gate == 0) return;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) *b.aclose_ok = 1;   // the marks below are for these positions
     if (s >= b.N) return;
     const int gi = b.perm[s];
     const Inst &I = b.inst[b.pinst[gi]];
     const int ti = b.stype[s];
+    // mark particles with a mobile neighbour inside the collision radius of
+    // the artificial viscosity (a superset: the collision pass decides exactly)
+    const bool want_close = I.artvis && (ti == T_FLUID || ti == T_RIGID);
+    const R close_r2 = (R)(I.artvis_r2f_hi * 1.0001f);
+    bool close = false;
     double d;
     if (ti == T_OUTER) {
         d = I.inv_dx3;  // outer-wall particles are not updated (Section 2.5)
@@ -177,6 +183,10 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
             if (e & NB_FAR) continue;
             R rx, ry, rz, r2;
             if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
+            if (want_close && r2 <= close_r2) {
+                const int tj = mir_type(A[e]);
+                close |= (tj == T_FLUID || tj == T_RIGID);
+            }
             // float: correctly rounded sqrt; double: r2 / sqrt via rsqrt (~1 ulp)
             const R q = (sizeof(R) == 4 ? sqrt(r2) : r2 * rsqrt_<R>(r2)) * irc;
             const R om = q < R(1) ? R(1) - q : R(0);
@@ -187,6 +197,7 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
     const double rho = I.mf * d;
     double p = I.p0 * pow(rho / I.rho0, I.alpha) - I.beta_p;
     if (I.clamp && p < 0.0) p = 0.0;
+    b.aclose[s] = close ? 1 : 0;
     b.sd[s] = d;
     b.sp[s] = p;
     if (!any_filter) {
@@ -255,15 +266,35 @@ __device__ __forceinline__ double exact_disp(const double *xi, const double *xj,
     return __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
 }
 
-// Per rigid particle s (one warp each, lanes striding over its neighbour
-// list, order-fixed warp reduction): eps_s from the rigid volumes within h
+// The sphere kernels run one CTA of RB threads per rigid particle: the
+// threads stride over its neighbour list and the partial sums are reduced in
+// a fixed order (warp shuffles, then warps 0, 1, ... in thread 0), so the
+// result does not depend on scheduling.
+constexpr int RB = 128;
+
+template <int K>
+__device__ __forceinline__ void block_sum_to_t0(double (&v)[K], double (*red)[K])
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < K; ++a) v[a] = warp_sum(v[a]);
+    if (lane == 0)
+        for (int a = 0; a < K; ++a) red[w][a] = v[a];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int ww = 1; ww < RB / 32; ++ww)
+            for (int a = 0; a < K; ++a) v[a] += red[ww][a];
+}
+
+// Per rigid particle s (one CTA each, threads striding over its neighbour
+// list, order-fixed block reduction): eps_s from the rigid volumes within h
 // (s included), v_f = sum W v / sum W over fluid neighbours, drag along
 // (v_f - v_s) with the Ergun (eps <= 0.8) or Wen-Yu (eps > 0.8) coefficient in
 // the closed form that stays finite at eps -> 1 and |v_f - v_s| -> 0.
-__global__ void k_drag(Bufs b)
+__global__ void __launch_bounds__(RB) k_drag(Bufs b)
 {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    __shared__ double red[RB / 32][5];
+    const int r = blockIdx.x;
     if (r >= b.nrigid) return;
     const int g = b.rigid_gid[r];
     const long long s = b.slot_of[g];
@@ -272,7 +303,7 @@ __global__ void k_drag(Bufs b)
     const double Ri = b.R[g];
     double Vsum = 0.0, S = 0.0, U0 = 0.0, U1 = 0.0, U2 = 0.0;
     const int n = b.ncnt[s];
-    for (int k = lane; k < n; k += 32) {
+    for (int k = threadIdx.x; k < n; k += RB) {
         const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
         if (e & NB_FAR) continue;
         const int gj = b.perm[e];
@@ -293,12 +324,14 @@ __global__ void k_drag(Bufs b)
             U2 += W * b.v[3 * gj + 2];
         }
     }
-    Vsum = warp_sum(Vsum) + 4.0 / 3.0 * PI * Ri * Ri * Ri;
-    S = warp_sum(S);
-    U0 = warp_sum(U0);
-    U1 = warp_sum(U1);
-    U2 = warp_sum(U2);
-    if (lane != 0) return;
+    double sums[5] = { Vsum, S, U0, U1, U2 };
+    block_sum_to_t0(sums, red);
+    if (threadIdx.x != 0) return;
+    Vsum = sums[0] + 4.0 / 3.0 * PI * Ri * Ri * Ri;
+    S = sums[1];
+    U0 = sums[2];
+    U1 = sums[3];
+    U2 = sums[4];
     const double U[3] = { U0, U1, U2 };
     double eps = fabs(I.Vf - Vsum) / I.Vf;
     eps = fmin(fmax(eps, I.eps_min), 1.0);
@@ -826,10 +859,11 @@ __device__ __forceinline__ void hist_put(const Bufs &b, int r, int slot, int par
 // wall planes, drag, gravity.  Lanes stride over the neighbour list in rounds
 // of 32; new history entries go to round-major, lane-minor slots (ballot),
 // so the table is deterministic.
-__global__ void k_force_rigid(Bufs b, int velver)
+__global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
 {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    __shared__ double red[RB / 32][15];
+    const int r = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (r >= b.nrigid) return;
     const int g = b.rigid_gid[r];
     const long long s = b.slot_of[g];
@@ -845,69 +879,83 @@ __global__ void k_force_rigid(Bufs b, int velver)
     for (int a = 0; a < 15; ++a) acc[a] = 0.0;   // pg, npg, Fdem, Tdem, Flub
     int base = 0;
     const int n = b.ncnt[s];
-    for (int kk = 0; kk < n; kk += 32) {
-        const int k = kk + lane;
-        bool contact = false;
-        int partner = 0;
-        double dn[3] = { 0.0, 0.0, 0.0 };
-        if (k < n) {
-            const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
-            const int j = (int)(e & ~NB_FAR);
-            const int gj = b.perm[j];
-            const int tj = b.type[gj];
-            const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-            double rv[3];
-            const double r2 = exact_disp(xi, xj, I, rv);
-            const double L = sqrt(r2);
-            const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
-            if (tj == T_FLUID && !(e & NB_FAR) && r2 < I.rc2) {
-                // F^C + F^D of the pair (s, j), summed for Eq. F_fpi_PG
-                const double ex = rv[0] / L, ey = rv[1] / L, ez = rv[2] / L;
-                const double q = L / I.rc, om = 1.0 - q;
-                const double Fk = I.Fc * om * om;
-                const double dj = b.sd[j];
-                const double fc = I.coeff_c * (Pi + b.sp2[j] / (dj * dj)) * Fk;
-                const double gf = Fk / (di * dj);
-                const double ga = I.Ca * gf, gb = I.Cb * gf;
-                const double ev = ex * vij[0] + ey * vij[1] + ez * vij[2];
-                double f[3];
-                const double e3[3] = { ex, ey, ez };
-                for (int a = 0; a < 3; ++a)
-                    f[a] = fc * rv[a] + I.coeff_d * (-ga * (vij[a] + e3[a] * ev / 3.0) - 2.0 * gb / 3.0 * e3[a] * ev);
-                double lev[3] = { -Ri * ex, -Ri * ey, -Ri * ez }, tq[3];
-                cross3(lev, f, tq);
-                for (int a = 0; a < 3; ++a) {
-                    acc[a] += f[a];
-                    acc[3 + a] += tq[a];
-                }
-            } else if (tj == T_RIGID) {
-                const double Rj = b.R[gj];
-                const double dsum = Ri + Rj;
-                if (L < dsum) {
-                    const double nn[3] = { rv[0] / L, rv[1] / L, rv[2] / L };
-                    double wsR[3];
-                    for (int a = 0; a < 3; ++a) wsR[a] = Ri * wi[a] + Rj * b.w[3 * gj + a];
-                    double kn, kt, cn, ct;
-                    dem_coeffs(I, Ri, Rj, mi, b.m[gj], kn, kt, cn, ct);
-                    dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
-                    contact = true;
-                    partner = gj;
-                } else if (r2 < I.rc2) {
-                    double gap = L - dsum;
-                    const double gmin = I.lub_gap_min * dsum;
-                    if (gap < gmin) gap = gmin;
-                    const double c = 3.0 * PI * I.eta * dsum * dsum / (8.0 * gap);
-                    for (int a = 0; a < 3; ++a) acc[12 + a] += c * (-vij[a]);
+    // fluid neighbours: F^C + F^D of each pair (s, j), summed for Eq. F_fpi_PG
+    for (int k = threadIdx.x; k < n; k += RB) {
+        const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
+        if (e & NB_FAR) continue;
+        const int j = (int)e;
+        const int gj = b.perm[j];
+        if (b.type[gj] != T_FLUID) continue;
+        const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+        double rv[3];
+        const double r2 = exact_disp(xi, xj, I, rv);
+        if (!(r2 < I.rc2)) continue;
+        const double L = sqrt(r2), iL = 1.0 / L;
+        const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
+        const double ex = rv[0] * iL, ey = rv[1] * iL, ez = rv[2] * iL;
+        const double q = L / I.rc, om = 1.0 - q;
+        const double Fk = I.Fc * om * om;
+        const double dj = b.sd[j];
+        const double fc = I.coeff_c * (Pi + b.sp2[j] / (dj * dj)) * Fk;
+        const double gf = Fk / (di * dj);
+        const double ga = I.Ca * gf, gb = I.Cb * gf;
+        const double ev = ex * vij[0] + ey * vij[1] + ez * vij[2];
+        double f[3];
+        const double e3[3] = { ex, ey, ez };
+        for (int a = 0; a < 3; ++a)
+            f[a] = fc * rv[a] + I.coeff_d * (-ga * (vij[a] + e3[a] * ev * (1.0 / 3.0)) - gb * (2.0 / 3.0) * e3[a] * ev);
+        double lev[3] = { -Ri * ex, -Ri * ey, -Ri * ez }, tq[3];
+        cross3(lev, f, tq);
+        for (int a = 0; a < 3; ++a) {
+            acc[a] += f[a];
+            acc[3 + a] += tq[a];
+        }
+    }
+    // rigid neighbours (warp 0): DEM contact with its history slot in
+    // ballot order, or lubrication
+    if (warp == 0) {
+        for (int kk = 0; kk < n; kk += 32) {
+            const int k = kk + lane;
+            bool contact = false;
+            int partner = 0;
+            double dn[3] = { 0.0, 0.0, 0.0 };
+            if (k < n) {
+                const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
+                const int j = (int)(e & ~NB_FAR);
+                const int gj = b.perm[j];
+                if (b.type[gj] == T_RIGID) {
+                    const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+                    double rv[3];
+                    const double r2 = exact_disp(xi, xj, I, rv);
+                    const double L = sqrt(r2);
+                    const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
+                    const double Rj = b.R[gj];
+                    const double dsum = Ri + Rj;
+                    if (L < dsum) {
+                        const double nn[3] = { rv[0] / L, rv[1] / L, rv[2] / L };
+                        double wsR[3];
+                        for (int a = 0; a < 3; ++a) wsR[a] = Ri * wi[a] + Rj * b.w[3 * gj + a];
+                        double kn, kt, cn, ct;
+                        dem_coeffs(I, Ri, Rj, mi, b.m[gj], kn, kt, cn, ct);
+                        dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
+                        contact = true;
+                        partner = gj;
+                    } else if (r2 < I.rc2) {
+                        double gap = L - dsum;
+                        const double gmin = I.lub_gap_min * dsum;
+                        if (gap < gmin) gap = gmin;
+                        const double c = 3.0 * PI * I.eta * dsum * dsum / (8.0 * gap);
+                        for (int a = 0; a < 3; ++a) acc[12 + a] += c * (-vij[a]);
+                    }
                 }
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, contact);
+            if (commit && contact) hist_put(b, r, base + __popc(bal & ((1u << lane) - 1u)), partner, dn);
+            base += __popc(bal);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, contact);
-        if (commit && contact) hist_put(b, r, base + __popc(bal & ((1u << lane) - 1u)), partner, dn);
-        base += __popc(bal);
     }
-#pragma unroll
-    for (int a = 0; a < 15; ++a) acc[a] = warp_sum(acc[a]);
-    if (lane != 0) return;
+    block_sum_to_t0(acc, red);
+    if (threadIdx.x != 0) return;
     // contact with the planes bounding the domain on wall axes
     for (int a = 0; a < 3; ++a) {
         if (I.periodic[a]) continue;
@@ -967,7 +1015,7 @@ void launch_density(const Bufs &b, int precision, int any_filter, const int *gat
 
 void launch_drag(const Bufs &b, cudaStream_t st)
 {
-    if (b.nrigid) k_drag<<<nblk(32LL * b.nrigid, 128), 128, 0, st>>>(b);
+    if (b.nrigid) k_drag<<<b.nrigid, RB, 0, st>>>(b);
 }
 
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st)
@@ -987,7 +1035,7 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
         k_force_fluid<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
     }
     if (b.nrigid) {
-        k_force_rigid<<<nblk(32LL * b.nrigid, 128), 128, 0, st>>>(b, velver);
+        k_force_rigid<<<b.nrigid, RB, 0, st>>>(b, velver);
         if (velver == 2) k_hist_copy<<<nblk(b.nrigid, 64), 64, 0, st>>>(b);
     }
 }

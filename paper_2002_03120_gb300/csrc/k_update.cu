@@ -37,6 +37,7 @@ template <class R>
 __global__ void k_integrate(Bufs b, int velver)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (velver == 1 && s == 0) *b.aclose_ok = 0;   // the drift moves the particles
     if (s >= b.N) return;
     const int g = b.perm[s];
     const int t = b.type[g];
@@ -115,7 +116,10 @@ __global__ void k_artvis(Bufs b)
     const int t = b.type[g];
     double dv[3] = { 0.0, 0.0, 0.0 };
     const Inst &I = b.inst[b.pinst[g]];
-    if ((t == T_FLUID || t == T_RIGID) && I.artvis) {
+    // the density pass of these positions marked the particles that have a
+    // mobile neighbour inside the collision radius; the others skip the scan
+    const bool marked = !*b.aclose_ok || b.aclose[s];
+    if ((t == T_FLUID || t == T_RIGID) && I.artvis && marked) {
         const double xi[3] = { b.x[3 * g], b.x[3 * g + 1], b.x[3 * g + 2] };
         const double vi[3] = { b.v[3 * g], b.v[3 * g + 1], b.v[3 * g + 2] };
         const double mi = b.m[g];
