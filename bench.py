@@ -47,6 +47,10 @@ WORKLOADS = {
 # algorithmic flops of one evaluation of one unordered pair by the force pass
 # (Eqs. FijC, FijD, FijR, FijT incl. Box-Muller; transcendentals counted as 1)
 FLOPS_PER_PAIR = 160.0
+# algorithmic bytes of the velver-1 update (kick + drift) of one mobile
+# particle: read x, v, w, F, N (5 x 24 B) and m, I (2 x 8 B), write x, v, w
+# (3 x 24 B)
+INTEGRATE_BYTES = 208.0
 # nominal ALU peaks from unit counts x maximum SM clock (152 SMs, 2070 MHz):
 # FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM, 2 flops per FMA
 FP64_PEAK_TF = 152 * 2 * 2 * 2070e6 / 1e12
@@ -191,6 +195,19 @@ def time_native(args, ws, rank, local):
             b.record(stream)
             b.synchronize()
             fms.append(a.elapsed_time(b))
+        # the HBM-bound update kernel alone (velocity Verlet, velver 1: kick
+        # and drift; the velver-2 call also runs the collision pass)
+        ims = []
+        for _ in range(5):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.integrate(1, stream)
+            b.record(stream)
+            b.synchronize()
+            ims.append(a.elapsed_time(b))
         # end-to-end through the C ABI with host buffers: upload the step's
         # state from pinned memory, run the step, read the result back
         N = sim.N
@@ -212,8 +229,10 @@ def time_native(args, ws, rank, local):
             b.record(stream)
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
+        mobile = int(sum(int(np.sum(c["type"] <= 1)) for c in sim.cases))
         out = dict(pairs=pairs, ms=total_ms, per_step=ms, kernels=kernels,
                    force_ms=float(np.median(fms)), e2e_ms=float(np.mean(e2e_ms)),
+                   integrate_ms=float(np.median(ims)), mobile=mobile,
                    e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N)
         sim.close()
         return out
@@ -469,6 +488,16 @@ def main():
                      "note": ("peak = %s nominal from unit counts x max clock (2070 MHz); "
                               "achieved counts 160 flop per unordered pair; traffic = ncu DRAM "
                               "bytes of %s per launch (profiles/)") % ("FP64" if fp64 else "FP32", main_k)},
+        "hbm_kernel": {"kernel": "k_integrate (velver 1: kick + drift)", "bound": "hbm",
+                       "achieved": main_r["mobile"] * INTEGRATE_BYTES / (main_r["integrate_ms"] / 1e3) / 1e9,
+                       "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                       "frac": (main_r["mobile"] * INTEGRATE_BYTES / (main_r["integrate_ms"] / 1e3) / 1e9
+                                / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
+                       "bytes_per_particle": INTEGRATE_BYTES, "particles": main_r["mobile"],
+                       "ms_per_launch": main_r["integrate_ms"],
+                       "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json); the kernel also "
+                               "keeps the cell-relative mirrors current (xl64, dsp, A32, A64: about 190 B "
+                               "more per particle), which the algorithmic bytes do not count"},
         "e2e": {"value": pairs * 2 / (main_r["e2e_ms"] / 1e3) * ws, "unit": UNIT,
                 "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
         "split_precision" if fp64 else "fp64_path": None if other_r is None else {

@@ -329,7 +329,7 @@ void set_last_error(const char *msg);
 // (defined in k_cells.cu, k_pairs.cu, k_update.cu; all enqueue on `st`)
 // gate: nullptr = always build; else build only when *gate != 0
 void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, cudaStream_t st);
-void launch_density(const Bufs &b, int precision, int any_filter, const int *gate, cudaStream_t st);
+void launch_density(const Bufs &b, int precision, int any_filter, int newton3, const int *gate, cudaStream_t st);
 void launch_drag(const Bufs &b, cudaStream_t st);
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st);
 void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st);

@@ -206,6 +206,108 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
     }
 }
 
+// FP64 density with each unordered pair evaluated once (Newton 3): phase 1
+// sums W over the owned prefix of the list and stores each W for the partner
+// (negated when the pair lies inside the collision radius of the artificial
+// viscosity; 0 for pairs beyond h) in the pair buffer, which is free between
+// force passes; phase 2 adds the partners' values read through the reverse
+// index.  The partner's r_ji = -r_ij bit for bit and the terms are summed in
+// list order ([owned][not owned]) as in k_density, so the result is the same.
+__global__ void __launch_bounds__(256) k_density_half(Bufs b, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) *b.aclose_ok = 1;
+    if (s >= b.N) return;
+    const int gi = b.perm[s];
+    const Inst &I = b.inst[b.pinst[gi]];
+    const int ti = b.stype[s];
+    const double4_32a *A = Mir<double>::A(b);
+    const double4_32a Ai = A[s];
+    const Geo<double> geo(I);
+    const int nf = b.nfirst[s];
+    const long long Np = b.Npad;
+    double *__restrict__ wb = (double *)b.resB;
+    const double close_r2 = (double)(I.artvis_r2f_hi * 1.0001f);
+    const bool want_close = I.artvis != 0;
+    bool close = false;
+    double acc = I.W0;
+    for (int k = 0; k < nf; ++k) {
+        const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
+        double W = 0.0;
+        if (!(e & NB_FAR)) {
+            double rx, ry, rz, r2;
+            if (Rel<double>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) {
+                const double q = r2 * rsqrt_<double>(r2) * K<double>::inv_rc(I);
+                const double om = q < 1.0 ? 1.0 - q : 0.0;
+                W = K<double>::Wc(I) * (1.0 + 3.0 * q) * om * om * om;
+                acc += W;
+                if (want_close && r2 <= close_r2) {
+                    const int tj = mir_type(A[e]);
+                    const bool mob = (tj == T_FLUID || tj == T_RIGID);
+                    if (mob && (ti == T_FLUID || ti == T_RIGID)) {
+                        close = true;
+                        W = -W;   // tells the partner
+                    }
+                }
+            }
+        }
+        wb[(long long)k * Np + s] = W;
+    }
+    b.sd[s] = acc;   // partial; completed by k_density_gather
+    b.aclose[s] = close ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256) k_density_gather(Bufs b, int any_filter, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.N) return;
+    const int gi = b.perm[s];
+    const Inst &I = b.inst[b.pinst[gi]];
+    const int ti = b.stype[s];
+    double d;
+    if (ti == T_OUTER) {
+        d = I.inv_dx3;  // outer-wall particles are not updated (Section 2.5)
+    } else {
+        const double *__restrict__ wb = (const double *)b.resB;
+        const int n = b.ncnt[s], nf = b.nfirst[s];
+        const long long Np = b.Npad;
+        const uint16_t *__restrict__ rv = b.rev + s;
+        double acc = b.sd[s];
+        bool close = b.aclose[s] != 0;
+        constexpr int G = 4;
+        for (int k0 = nf; k0 < n; k0 += G) {
+            double w[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int k = k0 + g;
+                w[g] = 0.0;
+                if (k < n) {
+                    const uint32_t e = (uint32_t)__ldg(b.nbr + (long long)k * Np + s);
+                    if (!(e & NB_FAR)) w[g] = wb[(long long)__ldg(rv + (long long)k * Np) * Np + e];
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (w[g] < 0.0) close = true;
+                acc += fabs(w[g]);
+            }
+        }
+        d = I.Cn * acc;
+        b.aclose[s] = (close && (ti == T_FLUID || ti == T_RIGID)) ? 1 : 0;
+    }
+    const double rho = I.mf * d;
+    double p = I.p0 * pow(rho / I.rho0, I.alpha) - I.beta_p;
+    if (I.clamp && p < 0.0) p = 0.0;
+    b.sd[s] = d;
+    b.sp[s] = p;
+    if (!any_filter) {
+        b.sp2[s] = p;
+        finalize_slot<double>(b, s, d, p);
+    }
+}
+
 // ------------------------------------------------------------ pressure filter
 template <class R>
 __global__ void __launch_bounds__(256) k_filter(Bufs b, const int *gate)
@@ -1001,10 +1103,14 @@ __global__ void k_hist_copy(Bufs b)
 // ---------------------------------------------------------------- launchers
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-void launch_density(const Bufs &b, int precision, int any_filter, const int *gate, cudaStream_t st)
+void launch_density(const Bufs &b, int precision, int any_filter, int newton3, const int *gate, cudaStream_t st)
 {
     if (!b.N) return;
-    if (precision == SDPD_PREC_SPLIT) {
+    if (precision == SDPD_PREC_FP64 && newton3) {
+        k_density_half<<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
+        k_density_gather<<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+        if (any_filter) k_filter<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
+    } else if (precision == SDPD_PREC_SPLIT) {
         k_density<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
         if (any_filter) k_filter<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     } else {
