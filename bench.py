@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--paths", default="both", choices=["both", "main"],
                     help="also time the other precision path (both) or not")
     ap.add_argument("--max-neighbors", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (force variant, skin, block size) and use the defaults")
     return ap.parse_args()
 
 
@@ -154,7 +156,13 @@ def time_native(args, ws, rank, local):
     prec = B.SDPD_PREC_FP64 if args.precision == "fp64" else B.SDPD_PREC_SPLIT
 
     def run_path(precision):
+        setting = None
+        if not args.no_tune:
+            from paper_2002_03120_gb300 import autotune
+            setting = autotune.tune(case, precision=precision, max_neighbors=args.max_neighbors)
         sim = B.Sim(case, precision=precision, max_neighbors=args.max_neighbors)
+        if setting:
+            autotune.apply(sim, setting)
         sim.build_cells(stream)
         torch.cuda.synchronize()
         pairs = sim.count_pairs()
@@ -232,7 +240,7 @@ def time_native(args, ws, rank, local):
         mobile = int(sum(int(np.sum(c["type"] <= 1)) for c in sim.cases))
         out = dict(pairs=pairs, ms=total_ms, per_step=ms, kernels=kernels,
                    force_ms=float(np.median(fms)), e2e_ms=float(np.mean(e2e_ms)),
-                   integrate_ms=float(np.median(ims)), mobile=mobile,
+                   integrate_ms=float(np.median(ims)), mobile=mobile, setting=setting,
                    e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N)
         sim.close()
         return out
@@ -475,7 +483,8 @@ def main():
         "config": {"workload": WORKLOADS[args.workload], "particles": main_r["N"], "pairs_per_eval": pairs,
                    "evals_per_step": 2, "precision": args.precision,
                    "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}",
+                   "tuning": main_r["setting"] or "defaults (newton3 1, skin 0.03, block 256)"},
         "timesteps_per_s": steps_per_s,
         "gpu_launches": main_r["kernels"] * args.steps,
         "clocks": main_r["clocks"],
@@ -502,7 +511,7 @@ def main():
                 "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
         "split_precision" if fp64 else "fp64_path": None if other_r is None else {
             "value": other_val, "unit": UNIT, "ms_per_step": other_r["ms"] / args.steps,
-            "force_ms_per_launch": other_r["force_ms"],
+            "force_ms_per_launch": other_r["force_ms"], "tuning": other_r["setting"],
             "speedup_vs_fp64": (other_val / (value / ws)) if fp64 else None,
             "roofline": {"bound": "alu", "achieved": other_tf,
                          "peak": FP32_PEAK_TF if fp64 else FP64_PEAK_TF, "unit": "TFLOP/s",

@@ -442,7 +442,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     IALLOC(b.x, n3); IALLOC(b.v, n3); IALLOC(b.w, n3); IALLOC(b.F, n3); IALLOC(b.T, n3);
     IALLOC(b.dv, n3);
     IALLOC(b.type, N); IALLOC(b.pinst, N);
-    IALLOC(b.R, N); IALLOC(b.m, N); IALLOC(b.Iner, N);
+    IALLOC(b.R, N); IALLOC(b.m, N); IALLOC(b.Iner, N); IALLOC(b.rm, N); IALLOC(b.rI, N);
     IALLOC(b.key, N); IALLOC(b.slot_in_cell, N); IALLOC(b.tmp_perm, N); IALLOC(b.perm, N);
     IALLOC(b.slot_of, N); IALLOC(b.stype, N);
     IALLOC(b.sd, N); IALLOC(b.sp, N); IALLOC(b.sp2, N);
@@ -579,6 +579,15 @@ sdpd_status sdpd_set_particles(sdpd_ctx *c, int inst, long long n, const double 
         CUDA_TRY(cudaMemcpy(b.R + o, hR.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(b.m + o, hm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(b.Iner + o, hI.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        // correctly rounded reciprocals (IEEE division on the host) for the
+        // update's divisions by m and I
+        std::vector<double> hrm(n), hrI(n);
+        for (long long i = 0; i < n; ++i) {
+            hrm[i] = hm[i] != 0.0 ? 1.0 / hm[i] : 0.0;
+            hrI[i] = hI[i] != 0.0 ? 1.0 / hI[i] : 0.0;
+        }
+        CUDA_TRY(cudaMemcpy(b.rm + o, hrm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.rI + o, hrI.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemset(b.F + 3 * o, 0, sizeof(double) * n3));
         CUDA_TRY(cudaMemset(b.T + 3 * o, 0, sizeof(double) * n3));
     }

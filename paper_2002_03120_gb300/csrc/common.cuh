@@ -87,6 +87,7 @@ struct Bufs {
     uint16_t *rev;             // non-owned entry k of s -> position of s in the partner's list
     uint8_t *nbflag;           // per slot: bit 0 = has a rigid neighbour
     int capown;                // owned entries per particle in the pair buffer
+    double *rm, *rI;           // [N] 1/m and 1/I rounded to nearest (the update divides with them)
     uint8_t *aclose;           // [N] slot has a mobile neighbour within the collision radius
     int *aclose_ok;            // the marks belong to the current positions and list
     void *resA, *resB;         // pair results [capown][Npad]: FP64 R4 {f, h.x}, R2 {h.y, h.z}

@@ -134,7 +134,8 @@ template <> struct Acc<float> {
 template <> struct Acc<double> {
     double s;
     __device__ __forceinline__ explicit Acc(double v0) : s(v0) {}
-    __device__ __forceinline__ void add(double v) { s += v; }
+    // a separate rounding of each term (no multiply-add fused into the sum)
+    __device__ __forceinline__ void add(double v) { s = __dadd_rn(s, v); }
     __device__ __forceinline__ double value() const { return s; }
 };
 
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(256) k_density_half(Bufs b, const int *gate)
                 const double q = r2 * rsqrt_<double>(r2) * K<double>::inv_rc(I);
                 const double om = q < 1.0 ? 1.0 - q : 0.0;
                 W = K<double>::Wc(I) * (1.0 + 3.0 * q) * om * om * om;
-                acc += W;
+                acc = __dadd_rn(acc, W);
                 if (want_close && r2 <= close_r2) {
                     const int tj = mir_type(A[e]);
                     const bool mob = (tj == T_FLUID || tj == T_RIGID);
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(256) k_density_gather(Bufs b, int any_filter, 
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (w[g] < 0.0) close = true;
-                acc += fabs(w[g]);
+                acc = __dadd_rn(acc, fabs(w[g]));
             }
         }
         d = I.Cn * acc;

@@ -33,6 +33,18 @@ __device__ __forceinline__ void write_vel_mirror(const Bufs &b, long long s, con
 // velver 1 also drifts x += dt v, wraps periodic axes and mirrors particles
 // that crossed a wall plane (normal velocity reversed).  The arithmetic is
 // written without fused multiply-adds so it repeats the oracle bit for bit.
+// a / d rounded to nearest from y = RN(1/d) by Markstein's method (P.
+// Markstein, IBM J. Res. Dev. 34, 1990): q0 = RN(a y), the remainder
+// r = a - d q0 is exact with a fused multiply-add, and RN(q0 + r y) is the
+// correctly rounded quotient (no overflow or underflow here): the result of
+// the division a / d, with one multiply and two multiply-adds.
+__device__ __forceinline__ double div_rn(double a, double d, double y)
+{
+    const double q0 = __dmul_rn(a, y);
+    const double r = __fma_rn(-q0, d, a);
+    return __fma_rn(r, y, q0);
+}
+
 template <class R>
 __global__ void k_integrate(Bufs b, int velver)
 {
@@ -43,13 +55,13 @@ __global__ void k_integrate(Bufs b, int velver)
     const int t = b.type[g];
     if (t != T_FLUID && t != T_RIGID) return;
     const Inst &I = b.inst[b.pinst[g]];
-    const double im = b.m[g], iI = b.Iner[g];
+    const double im = b.m[g], iI = b.Iner[g], rm = b.rm[g], rI = b.rI[g];
     double v[3], w[3], x[3];
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        v[a] = __dadd_rn(b.v[3 * g + a], __dmul_rn(I.hdt, __ddiv_rn(b.F[3 * g + a], im)));
-        w[a] = __dadd_rn(b.w[3 * g + a], __dmul_rn(I.hdt, __ddiv_rn(b.T[3 * g + a], iI)));
+        v[a] = __dadd_rn(b.v[3 * g + a], __dmul_rn(I.hdt, div_rn(b.F[3 * g + a], im, rm)));
+        w[a] = __dadd_rn(b.w[3 * g + a], __dmul_rn(I.hdt, div_rn(b.T[3 * g + a], iI, rI)));
     }
     if (velver == 1) {
         double dl[3];
