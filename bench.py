@@ -349,11 +349,14 @@ def time_surrogate(args, ws, rank, local):
 
 
 def max_over_ranks(v, ws):
+    """The largest value over the ranks (the job's time is its slowest
+    rank's)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -484,7 +487,7 @@ def main():
                    "evals_per_step": 2, "precision": args.precision,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{ws}",
-                   "tuning": main_r["setting"] or "defaults (newton3 1, skin 0.03, block 256)"},
+                   "tuning": main_r["setting"] or "defaults (newton3 1, skin 0.03, block 128)"},
         "timesteps_per_s": steps_per_s,
         "gpu_launches": main_r["kernels"] * args.steps,
         "clocks": main_r["clocks"],

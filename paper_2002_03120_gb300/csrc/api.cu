@@ -484,7 +484,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         b.zA = za; b.zB = zb;
     }
     b.use_cache = 1;
-    IALLOC(b.step, 1); IALLOC(b.err, 1); IALLOC(b.pair_count, 1);
+    IALLOC(b.step, 1); IALLOC(b.err, 1); IALLOC(b.pair_count, 1); IALLOC(b.work, 1);
     IALLOC(b.probe, 4096 * 2 + 64);
 #undef IALLOC
     if (cudaMemset(b.need_build, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.fresh, 0, sizeof(int)) != cudaSuccess ||

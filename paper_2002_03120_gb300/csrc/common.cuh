@@ -115,6 +115,7 @@ struct Bufs {
     long long *step;
     int *err;
     unsigned long long *pair_count;
+    unsigned long long *work;  // slot counter of the persistent pair kernels
     double *probe;             // scratch for probe / diagnostics
 };
 

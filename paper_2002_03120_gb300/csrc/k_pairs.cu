@@ -19,6 +19,7 @@
 // every sum has a fixed order.  The random matrix of a pair is regenerated
 // from the counter (min gid, max gid, step) or, in the second evaluation of a
 // step, read back from the first one's cache (same counter, same bits).
+#include <algorithm>
 #include "common.cuh"
 
 namespace sdpd {
@@ -489,6 +490,17 @@ template <class R> struct PairK {
           key0(I.key0), key1(I.key1) {}
 };
 
+// Persistent pair kernels: each warp takes the next 32 slots from a counter
+// (zeroed before the launch) until none are left, so that no SM idles in the
+// tail of a partial last wave.  The result of a slot does not depend on
+// which warp computes it.
+__device__ __forceinline__ long long next_warp_slots(const Bufs &b)
+{
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(b.work, 32ull);
+    return (long long)__shfl_sync(0xffffffffu, base, 0);
+}
+
 template <class R> struct Z6 {
     R z0, z1, z2, z3, z4, z5;
 };
@@ -585,10 +597,9 @@ __device__ __forceinline__ void write_fluid_force(const Bufs &b, const Inst &I, 
 // particle i; the next neighbour's records are fetched before the current
 // pair is evaluated.
 template <class R>
-__global__ void __launch_bounds__(256) k_force_fluid(Bufs b)
+__device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s)
 {
     using T4 = typename Vec<R>::T4;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     if (b.stype[s] != T_FLUID) return;
     const int gi = b.perm[s];
@@ -639,6 +650,13 @@ __global__ void __launch_bounds__(256) k_force_fluid(Bufs b)
     write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, P.lev);
 }
 
+template <class R>
+__global__ void __launch_bounds__(256) k_force_fluid(Bufs b)
+{
+    for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+        force_fluid_slot<R>(b, base + (threadIdx.x & 31));
+}
+
 // Newton-3 force pass, phase 1: every fluid or wall particle evaluates the
 // pairs of its owned prefix (see k_neighbors; within h, both non-rigid, at
 // least one fluid) once, stores (f, e x o) in its own column of the pair
@@ -647,19 +665,11 @@ __global__ void __launch_bounds__(256) k_force_fluid(Bufs b)
 // six normals of each pair; the second reads them back when the list has not
 // been rebuilt in between (same counter, so the same bits).
 template <class R>
-__global__ void __launch_bounds__(256) k_force_half(Bufs b, int velver)
+__device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint32_t step, bool fill,
+                                                bool reuse)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t step = (uint32_t)(*b.step);
-    const bool fill = b.use_cache && velver == 1;
-    const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
-                       *b.cache_step == *b.step;
-    if (fill && s == 0) {
-        *b.cache_epoch = *b.list_epoch;
-        *b.cache_step = *b.step;
-    }
     if (s >= b.N) return;
     const int ti = b.stype[s];
     if (ti == T_RIGID) return;
@@ -747,6 +757,23 @@ __global__ void __launch_bounds__(256) k_force_half(Bufs b, int velver)
         ((T4 *)b.ownA)[s] = oa;
         ((T2 *)b.ownB)[s] = ob;
     }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_force_half(Bufs b, int velver)
+{
+    const uint32_t step = (uint32_t)(*b.step);
+    const bool fill = b.use_cache && velver == 1;
+    const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
+                       *b.cache_step == *b.step;
+    // every warp reads the epochs before the first one is written below
+    __syncthreads();
+    if (fill && blockIdx.x == 0 && threadIdx.x == 0) {
+        *b.cache_epoch = *b.list_epoch;
+        *b.cache_step = *b.step;
+    }
+    for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+        force_half_slot<R>(b, base + (threadIdx.x & 31), step, fill, reuse);
 }
 
 // Newton-3 force pass, phase 2 (fluid particles): own sum + the stored
@@ -1125,21 +1152,37 @@ void launch_drag(const Bufs &b, cudaStream_t st)
     if (b.nrigid) k_drag<<<b.nrigid, RB, 0, st>>>(b);
 }
 
+// Blocks of a persistent launch: as many as are resident at once (never
+// more than the warps needed to cover N).
+template <class K>
+static unsigned persistent_grid(K kernel, int block, long long N)
+{
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long need = (N + block - 1) / block;
+    return (unsigned)std::min<long long>(need, (long long)nsm * per_sm);
+}
+
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st)
 {
     if (!b.N) return;
+    const int bs = b.pair_block;
+    cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
     if (newton3) {
         if (precision == SDPD_PREC_SPLIT) {
-            k_force_half<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, velver);
-            k_force_gather<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
+            k_force_half<float><<<persistent_grid(k_force_half<float>, bs, b.N), bs, 0, st>>>(b, velver);
+            k_force_gather<float><<<nblk(b.N, bs), bs, 0, st>>>(b);
         } else {
-            k_force_half<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, velver);
-            k_force_gather<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
+            k_force_half<double><<<persistent_grid(k_force_half<double>, bs, b.N), bs, 0, st>>>(b, velver);
+            k_force_gather<double><<<nblk(b.N, bs), bs, 0, st>>>(b);
         }
     } else if (precision == SDPD_PREC_SPLIT) {
-        k_force_fluid<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
+        k_force_fluid<float><<<persistent_grid(k_force_fluid<float>, bs, b.N), bs, 0, st>>>(b);
     } else {
-        k_force_fluid<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b);
+        k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b);
     }
     if (b.nrigid) {
         k_force_rigid<<<b.nrigid, RB, 0, st>>>(b, velver);
