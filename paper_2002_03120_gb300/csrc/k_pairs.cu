@@ -152,6 +152,17 @@ __device__ __forceinline__ void finalize_slot(const Bufs &b, long long s, double
     D[s] = o;
 }
 
+// Persistent pair kernels: each warp takes the next 32 slots from a counter
+// (zeroed before the launch) until none are left, so that no SM idles in the
+// tail of a partial last wave.  The result of a slot does not depend on
+// which warp computes it.
+__device__ __forceinline__ long long next_warp_slots(const Bufs &b)
+{
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(b.work, 32ull);
+    return (long long)__shfl_sync(0xffffffffu, base, 0);
+}
+
 // ------------------------------------------------------------------ density
 // gate: nullptr = always; else only when *gate != 0 (a build just happened)
 template <class R>
@@ -215,11 +226,8 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
 // force passes; phase 2 adds the partners' values read through the reverse
 // index.  The partner's r_ji = -r_ij bit for bit and the terms are summed in
 // list order ([owned][not owned]) as in k_density, so the result is the same.
-__global__ void __launch_bounds__(256) k_density_half(Bufs b, const int *gate)
+__device__ __forceinline__ void density_half_slot(const Bufs &b, long long s)
 {
-    if (gate && *gate == 0) return;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s == 0) *b.aclose_ok = 1;
     if (s >= b.N) return;
     const int gi = b.perm[s];
     const Inst &I = b.inst[b.pinst[gi]];
@@ -258,6 +266,14 @@ __global__ void __launch_bounds__(256) k_density_half(Bufs b, const int *gate)
     }
     b.sd[s] = acc;   // partial; completed by k_density_gather
     b.aclose[s] = close ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256) k_density_half(Bufs b, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *b.aclose_ok = 1;
+    for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+        density_half_slot(b, base + (threadIdx.x & 31));
 }
 
 __global__ void __launch_bounds__(256) k_density_gather(Bufs b, int any_filter, const int *gate)
@@ -479,27 +495,24 @@ __device__ __forceinline__ void ext_accel(const Inst &I, const double *x, double
 
 // -------------------------------------------------------- fluid force pass
 // Constants of the SDPD pair force in precision R, held in registers.
+// Products of instance constants are folded once per thread:
+//   A1 = -cd Ca, A2 = cd (Ca + 2 Cb) / 3, A3 = -cr Ca / 2 (Eqs. FijD, FijR with
+//   gamma_a = Ca F/(d_i d_j), gamma_b = Cb F/(d_i d_j)); T1 = ct Ka / sqrt(dt),
+//   T3 = ct (Kb - Ka) / (3 sqrt(dt)) (Eq. FijT with sigma = K sqrt(F)/sqrt(d_i d_j)).
 template <class R> struct PairK {
-    R irc, Fc, Wc, Ca, Cb, Ka, Kb, cc, cd, cr, tn, lev;
+    R irc, Fc, Wc, cc, A1, A2, A3, T1, T3, lev;
     bool noise;
     uint32_t step, key0, key1;
     __device__ __forceinline__ PairK(const Inst &I, uint32_t st)
-        : irc(K<R>::inv_rc(I)), Fc(K<R>::Fc(I)), Wc(K<R>::Wc(I)), Ca(K<R>::Ca(I)), Cb(K<R>::Cb(I)),
-          Ka(K<R>::Ka(I)), Kb(K<R>::Kb(I)), cc(K<R>::cc(I)), cd(K<R>::cd(I)), cr(K<R>::cr(I)),
-          tn(K<R>::ct(I) * K<R>::isdt(I)), lev(K<R>::lever(I)), noise(I.noise != 0), step(st),
-          key0(I.key0), key1(I.key1) {}
+        : irc(K<R>::inv_rc(I)), Fc(K<R>::Fc(I)), Wc(K<R>::Wc(I)), cc(K<R>::cc(I)),
+          A1(-K<R>::cd(I) * K<R>::Ca(I)),
+          A2(K<R>::cd(I) * (K<R>::Ca(I) + R(2) * K<R>::Cb(I)) * R(1.0 / 3.0)),
+          A3(R(-0.5) * K<R>::cr(I) * K<R>::Ca(I)),
+          T1(K<R>::ct(I) * K<R>::isdt(I) * K<R>::Ka(I)),
+          T3(K<R>::ct(I) * K<R>::isdt(I) * (K<R>::Kb(I) - K<R>::Ka(I)) * R(1.0 / 3.0)),
+          lev(K<R>::lever(I)), noise(I.noise != 0), step(st), key0(I.key0), key1(I.key1) {}
 };
 
-// Persistent pair kernels: each warp takes the next 32 slots from a counter
-// (zeroed before the launch) until none are left, so that no SM idles in the
-// tail of a partial last wave.  The result of a slot does not depend on
-// which warp computes it.
-__device__ __forceinline__ long long next_warp_slots(const Bufs &b)
-{
-    unsigned long long base = 0;
-    if ((threadIdx.x & 31) == 0) base = atomicAdd(b.work, 32ull);
-    return (long long)__shfl_sync(0xffffffffu, base, 0);
-}
 
 template <class R> struct Z6 {
     R z0, z1, z2, z3, z4, z5;
@@ -541,7 +554,7 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R
                                           const T4 &Dj, bool with_rt, int zmode, Z6<R> &z, R &ox,
                                           R &oy, R &oz, R &ce, R &ex, R &ey, R &ez, R &q, R &om)
 {
-    const R third = R(1.0 / 3.0), is2 = R(0.70710678118654752440);
+    const R is2 = R(0.70710678118654752440);
     const R ir = rsqrt_<R>(r2);
     q = r2 * ir * P.irc;
     om = q < R(1) ? R(1) - q : R(0);
@@ -550,15 +563,14 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R
     const R vx = Bi.x - Bj.x, vy = Bi.y - Bj.y, vz = Bi.z - Bj.z;
     const R ev = ex * vx + ey * vy + ez * vz;
     const R gf = Fk * Di.y * Dj.y;
-    const R ga = P.Ca * gf, gb = P.Cb * gf;
-    const R c1 = -P.cd * ga;
+    const R c1 = P.A1 * gf;
     // Eq. FijC (central) + the central part of Eq. FijD
-    ce = P.cc * (Di.x + Dj.x) * Fk * (r2 * ir) - P.cd * (ga + R(2) * gb) * third * ev;
+    ce = P.cc * (Di.x + Dj.x) * Fk * (r2 * ir) - P.A2 * gf * ev;
     ox = c1 * vx; oy = c1 * vy; oz = c1 * vz;
     if (!with_rt) return;
     // Eq. FijR
     const R wx = Ci.x + Cj.x, wy = Ci.y + Cj.y, wz = Ci.z + Cj.z;
-    const R c3 = -P.cr * ga * R(0.5);
+    const R c3 = P.A3 * gf;
     ox += c3 * (ry * wz - rz * wy);
     oy += c3 * (rz * wx - rx * wz);
     oz += c3 * (rx * wy - ry * wx);
@@ -568,9 +580,9 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R
             pair_normals<R>(mir_gid(Di), mir_gid(Dj), P.step, P.key0, P.key1, z.z0, z.z1, z.z2, z.z3,
                             z.z4, z.z5);
         const R rs = om * Di.z * Dj.z;
-        const R sa = P.tn * P.Ka * rs, sb = P.tn * P.Kb * rs;
+        const R sa = P.T1 * rs;
         const R sxy = z.z3 * is2, sxz = z.z4 * is2, syz = z.z5 * is2;
-        ce += (sb - sa) * (z.z0 + z.z1 + z.z2) * third;
+        ce += P.T3 * rs * (z.z0 + z.z1 + z.z2);
         ox += sa * (z.z0 * ex + sxy * ey + sxz * ez);
         oy += sa * (sxy * ex + z.z1 * ey + syz * ez);
         oz += sa * (sxz * ex + syz * ey + z.z2 * ez);
@@ -1131,11 +1143,26 @@ __global__ void k_hist_copy(Bufs b)
 // ---------------------------------------------------------------- launchers
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Blocks of a persistent launch: as many as are resident at once (never
+// more than the warps needed to cover N).
+template <class K>
+static unsigned persistent_grid(K kernel, int block, long long N)
+{
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long need = (N + block - 1) / block;
+    return (unsigned)std::min<long long>(need, (long long)nsm * per_sm);
+}
+
 void launch_density(const Bufs &b, int precision, int any_filter, int newton3, const int *gate, cudaStream_t st)
 {
     if (!b.N) return;
     if (precision == SDPD_PREC_FP64 && newton3) {
-        k_density_half<<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
+        cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
+        k_density_half<<<persistent_grid(k_density_half, b.pair_block, b.N), b.pair_block, 0, st>>>(b, gate);
         k_density_gather<<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
         if (any_filter) k_filter<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     } else if (precision == SDPD_PREC_SPLIT) {
@@ -1152,19 +1179,6 @@ void launch_drag(const Bufs &b, cudaStream_t st)
     if (b.nrigid) k_drag<<<b.nrigid, RB, 0, st>>>(b);
 }
 
-// Blocks of a persistent launch: as many as are resident at once (never
-// more than the warps needed to cover N).
-template <class K>
-static unsigned persistent_grid(K kernel, int block, long long N)
-{
-    int dev = 0, nsm = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    const long long need = (N + block - 1) / block;
-    return (unsigned)std::min<long long>(need, (long long)nsm * per_sm);
-}
 
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st)
 {
