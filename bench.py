@@ -474,8 +474,13 @@ def main():
     force_flops = FLOPS_PER_PAIR * pairs
     achieved_tf = force_flops / (main_r["force_ms"] / 1e3) / 1e12
     other_tf = FLOPS_PER_PAIR * other_r["pairs"] / (other_r["force_ms"] / 1e3) / 1e12 if other_r else None
-    kd, kf = "k_force_half<double>", "k_force_half<float>"
-    main_k, other_k = (kd, kf) if fp64 else (kf, kd)
+    def force_kernel(res, double):
+        # the phase-1 kernel of the Newton-3 pass, or the direct pass
+        n3 = (res or {}).get("setting") or {}
+        name = "k_force_half" if n3.get("newton3", 1) else "k_force_fluid"
+        return f"{name}<{'double' if double else 'float'}>"
+    main_k = force_kernel(main_r, fp64)
+    other_k = force_kernel(other_r, not fp64)
     fp64_peak_tf = FP64_PEAK_TF if fp64 else FP32_PEAK_TF
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -491,15 +496,18 @@ def main():
         "timesteps_per_s": steps_per_s,
         "gpu_launches": main_r["kernels"] * args.steps,
         "clocks": main_r["clocks"],
-        "roofline": {"kernel": "force pass (k_force_half + k_force_gather + k_force_rigid), velver 1",
+        "roofline": {"kernel": ("force pass (k_force_half + k_force_gather + k_force_rigid), velver 1"
+                                if main_k.startswith("k_force_half") else
+                                "force pass (k_force_fluid + k_force_rigid), velver 1"),
                      "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / fp64_peak_tf,
                      "traffic": cnt.get(main_k, {}).get("dram_bytes_per_launch"),
                      "ms_per_launch": main_r["force_ms"],
                      "pipe_util_ncu": pipe_util(cnt.get(main_k), fp64),
                      "note": ("peak = %s nominal from unit counts x max clock (2070 MHz); "
-                              "achieved counts 160 flop per unordered pair; traffic = ncu DRAM "
-                              "bytes of %s per launch (profiles/)") % ("FP64" if fp64 else "FP32", main_k)},
+                              "achieved counts 160 flop per unordered pair (both directions of the "
+                              "direct pass count once); traffic = ncu DRAM bytes of %s per launch "
+                              "(profiles/)") % ("FP64" if fp64 else "FP32", main_k)},
         "hbm_kernel": {"kernel": "k_integrate (velver 1: kick + drift)", "bound": "hbm",
                        "achieved": main_r["mobile"] * INTEGRATE_BYTES / (main_r["integrate_ms"] / 1e3) / 1e9,
                        "peak": peaks.get("hbm_gbs"), "unit": "GB/s",

@@ -255,6 +255,21 @@ sdpd_status sdpd_density_noalloc(const sdpd_params *params, long long n, const d
 sdpd_status sdpd_noise_normals(int precision, unsigned long long seed, int inst, unsigned step, long long n,
                                const unsigned *gi, const unsigned *gj, double *z_out);
 
+/* Checkpoint and restart (the restart files of Section 3.1): the dynamic
+ * state of all instances -- positions, velocities and angular velocities
+ * [N][3] FP64 in particle order, the step counter (it keys the random
+ * stream) and the tangential contact histories of the rigid particles -- as
+ * one byte image in caller (host) memory.  sdpd_checkpoint_size gives its
+ * length; sdpd_checkpoint waits for the context and writes it; sdpd_restore
+ * reads it into a context of the same shape (same particle count, rigid
+ * particles and max_contacts; created from the same sdpd_set_particles data)
+ * and fails with SDPD_E_INVALID otherwise.  Both make the next step rebuild
+ * the neighbour lists, so a run restored from an image continues bit for bit
+ * as the run that wrote it. */
+sdpd_status sdpd_checkpoint_size(const sdpd_ctx *ctx, long long *bytes);
+sdpd_status sdpd_checkpoint(sdpd_ctx *ctx, void *buf, long long bytes);
+sdpd_status sdpd_restore(sdpd_ctx *ctx, const void *buf, long long bytes);
+
 /* Wait for all work of the context and report a pending kernel error. */
 sdpd_status sdpd_check(sdpd_ctx *ctx);
 

@@ -76,7 +76,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
            "sdpd_set_force_mode", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
            "sdpd_check",
-           "sdpd_last_error", "sdpd_noise_normals", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
+           "sdpd_last_error", "sdpd_noise_normals", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
            "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
 
 
@@ -126,6 +126,9 @@ def load(build_if_missing: bool = True):
         "sdpd_density_noalloc": (st, [C.POINTER(SdpdParams), C.c_longlong, vp, vp, vp, vp, vp]),
         "sdpd_check": (st, [vp]),
         "sdpd_last_error": (C.c_char_p, []),
+        "sdpd_checkpoint_size": (st, [vp, C.POINTER(C.c_longlong)]),
+        "sdpd_checkpoint": (st, [vp, vp, C.c_longlong]),
+        "sdpd_restore": (st, [vp, vp, C.c_longlong]),
         "sdpd_noise_normals": (st, [C.c_int, C.c_ulonglong, C.c_int, C.c_uint, C.c_longlong, vp, vp, vp]),
         "mlp_init": (st, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.POINTER(vp)]),
         "mlp_destroy": (None, [vp]),
@@ -286,6 +289,18 @@ class Sim:
         out = np.zeros(16)
         _check(load().sdpd_diagnostics(self._h, k, _dp(out)))
         return out
+
+    def checkpoint(self) -> np.ndarray:
+        """The dynamic state as a byte image (sdpd_checkpoint)."""
+        n = C.c_longlong()
+        _check(load().sdpd_checkpoint_size(self._h, C.byref(n)))
+        buf = np.zeros(n.value, dtype=np.uint8)
+        _check(load().sdpd_checkpoint(self._h, C.c_void_p(buf.ctypes.data), n.value))
+        return buf
+
+    def restore(self, image) -> None:
+        buf = np.ascontiguousarray(image, dtype=np.uint8)
+        _check(load().sdpd_restore(self._h, C.c_void_p(buf.ctypes.data), buf.size))
 
     def viscosity_probe(self, k: int = 0, n_bins: int = 32):
         prof = np.zeros(n_bins)

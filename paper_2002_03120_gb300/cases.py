@@ -167,6 +167,29 @@ def poiseuille_meso(nx=12, ny=24, nz=12, rho0=3.0, eta=25.0, amp=1.5, kBT=1.0, a
                      f"poiseuille_meso_{nx}x{ny}x{nz}")
 
 
+def poiseuille_meso_walls(nx=12, ny=24, nz=12, layers=4, **kw) -> dict:
+    """Reverse Poiseuille with the wall-periodic hybrid boundaries of Section
+    4.1: the mesoscale case of poiseuille_meso, but with dummy-particle walls
+    (`layers` layers, the first inner) on both faces of the split axis (y) and
+    periodic boundaries in x and z.  Each half is then a Poiseuille flow
+    between a wall and the mid-plane, read by the same Eq. poiseuave."""
+    case = poiseuille_meso(nx=nx, ny=ny, nz=nz, **kw)
+    p = case["params"]
+    p["periodic"] = [1, 0, 1]
+    dx = p["dx"]
+    wx, wt = _wall_layers((nx, ny, nz), dx, (0, 0, 0), layers, [(1, 0), (1, 1)])
+    nw = len(wx)
+    m = float(case["mass"][0])
+    case["x"] = np.concatenate([case["x"], wx])
+    case["type"] = np.concatenate([case["type"], wt])
+    case["radius"] = np.concatenate([case["radius"], np.full(nw, 0.5 * dx)])
+    case["mass"] = np.concatenate([case["mass"], np.full(nw, m)])
+    case["v"] = np.zeros_like(case["x"])
+    case["w"] = np.zeros_like(case["x"])
+    case["name"] = f"poiseuille_meso_walls_{nx}x{ny}x{nz}"
+    return case
+
+
 def _place_spheres_on_sites(nxyz, n_target: int, diam_dx: np.ndarray, periodic,
                             rng: np.random.Generator):
     """Random sequential addition on the sites of an nx x ny x nz lattice

@@ -624,6 +624,85 @@ sdpd_status sdpd_download_state(sdpd_ctx *c, double *x, double *v, double *w, do
     return SDPD_OK;
 }
 
+namespace {
+// checkpoint image: header, x v w [N][3] (gid order), contact histories
+struct CkptHeader {
+    uint32_t magic, version;
+    long long n, nrigid, K, step;
+};
+constexpr uint32_t CKPT_MAGIC = 0x4B434453u;  // "SDCK"
+long long ckpt_bytes(const sdpd_ctx *c)
+{
+    const long long nr = c->b.nrigid, K = c->K;
+    return (long long)sizeof(CkptHeader) + 9LL * c->N * (long long)sizeof(double) +
+           (nr + nr * K) * (long long)sizeof(int) + 3LL * nr * K * (long long)sizeof(double);
+}
+}  // namespace
+
+sdpd_status sdpd_checkpoint_size(const sdpd_ctx *c, long long *bytes)
+{
+    if (!c || !bytes) return fail(SDPD_E_INVALID, "sdpd_checkpoint_size: NULL argument");
+    *bytes = ckpt_bytes(c);
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_checkpoint(sdpd_ctx *c, void *buf, long long bytes)
+{
+    if (!c || !buf) return fail(SDPD_E_INVALID, "sdpd_checkpoint: NULL argument");
+    if (bytes < ckpt_bytes(c)) return fail(SDPD_E_INVALID, "sdpd_checkpoint: buffer too small");
+    CUDA_TRY(cudaDeviceSynchronize());
+    sdpd_status e = check_err(c);
+    if (e != SDPD_OK) return e;
+    char *p = (char *)buf;
+    CkptHeader h{ CKPT_MAGIC, 1u, c->N, c->b.nrigid, c->K, 0 };
+    CUDA_TRY(cudaMemcpy(&h.step, c->b.step, sizeof(long long), cudaMemcpyDeviceToHost));
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    const size_t n3 = sizeof(double) * 3 * (size_t)c->N;
+    CUDA_TRY(cudaMemcpy(p, c->b.x, n3, cudaMemcpyDeviceToHost)); p += n3;
+    CUDA_TRY(cudaMemcpy(p, c->b.v, n3, cudaMemcpyDeviceToHost)); p += n3;
+    CUDA_TRY(cudaMemcpy(p, c->b.w, n3, cudaMemcpyDeviceToHost)); p += n3;
+    const size_t nr = (size_t)c->b.nrigid, nk = nr * (size_t)c->K;
+    if (nr) {
+        CUDA_TRY(cudaMemcpy(p, c->b.h_n, sizeof(int) * nr, cudaMemcpyDeviceToHost)); p += sizeof(int) * nr;
+        CUDA_TRY(cudaMemcpy(p, c->b.h_part, sizeof(int) * nk, cudaMemcpyDeviceToHost)); p += sizeof(int) * nk;
+        CUDA_TRY(cudaMemcpy(p, c->b.h_del, sizeof(double) * 3 * nk, cudaMemcpyDeviceToHost));
+    }
+    // the next step rebuilds the lists, as it does after a restore, so both
+    // continuations sum the same terms in the same order
+    c->cells_valid = c->density_valid = c->drag_valid = false;
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_restore(sdpd_ctx *c, const void *buf, long long bytes)
+{
+    if (!c || !buf) return fail(SDPD_E_INVALID, "sdpd_restore: NULL argument");
+    if (bytes < (long long)sizeof(CkptHeader)) return fail(SDPD_E_INVALID, "sdpd_restore: image too small");
+    const char *p = (const char *)buf;
+    CkptHeader h;
+    std::memcpy(&h, p, sizeof h);
+    p += sizeof h;
+    if (h.magic != CKPT_MAGIC || h.version != 1u) return fail(SDPD_E_INVALID, "sdpd_restore: not a checkpoint image");
+    if (h.n != c->N || h.nrigid != c->b.nrigid || h.K != c->K)
+        return fail(SDPD_E_INVALID, "sdpd_restore: image of another context shape (particles, spheres, contacts)");
+    if (bytes < ckpt_bytes(c)) return fail(SDPD_E_INVALID, "sdpd_restore: image truncated");
+    CUDA_TRY(cudaDeviceSynchronize());
+    const size_t n3 = sizeof(double) * 3 * (size_t)c->N;
+    CUDA_TRY(cudaMemcpy(c->b.x, p, n3, cudaMemcpyHostToDevice)); p += n3;
+    CUDA_TRY(cudaMemcpy(c->b.v, p, n3, cudaMemcpyHostToDevice)); p += n3;
+    CUDA_TRY(cudaMemcpy(c->b.w, p, n3, cudaMemcpyHostToDevice)); p += n3;
+    const size_t nr = (size_t)c->b.nrigid, nk = nr * (size_t)c->K;
+    if (nr) {
+        CUDA_TRY(cudaMemcpy(c->b.h_n, p, sizeof(int) * nr, cudaMemcpyHostToDevice)); p += sizeof(int) * nr;
+        CUDA_TRY(cudaMemcpy(c->b.h_part, p, sizeof(int) * nk, cudaMemcpyHostToDevice)); p += sizeof(int) * nk;
+        CUDA_TRY(cudaMemcpy(c->b.h_del, p, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(cudaMemcpy(c->b.step, &h.step, sizeof(long long), cudaMemcpyHostToDevice));
+    c->host_step = h.step;
+    c->cells_valid = c->density_valid = c->drag_valid = false;
+    return SDPD_OK;
+}
+
 sdpd_status sdpd_set_step(sdpd_ctx *c, long long step)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");

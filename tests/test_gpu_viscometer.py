@@ -20,8 +20,9 @@ def _gpu():
     need_gpu()
 
 
-def _meso(eta=25.0, seed=1, amp=1.5):
-    c = cases.poiseuille_meso(nx=12, ny=24, nz=12, kBT=1e-3, eta=eta, amp=amp, seed=seed)
+def _meso(eta=25.0, seed=1, amp=1.5, walls=False):
+    make = cases.poiseuille_meso_walls if walls else cases.poiseuille_meso
+    c = make(nx=12, ny=24, nz=12, kBT=1e-3, eta=eta, amp=amp, seed=seed)
     p = c["params"]
     # acoustic limit, and the explicit friction limit of the dissipative pair
     # force (about 0.3 / eta at rho0 = 3, r_c = 3.9 dx)
@@ -62,3 +63,12 @@ def test_batched_viscometers_agree_with_single_runs():
         assert mus_b[k] == pytest.approx(e, rel=0.05), (k, mus_b[k], e)
     # viscosity ordering follows the input
     assert np.all(np.diff(mus_b) > 0)
+
+
+def test_wall_periodic_hybrid_agrees_with_fully_periodic():
+    # Section 4.1: with dummy-particle walls on the split axis and periodic x,
+    # z, the viscosity read-out differs from the fully periodic one by at most
+    # 2 % (the paper's statement)
+    mu_p = _steady_mu(B.Sim(_meso(), precision=B.SDPD_PREC_FP64))
+    mu_w = _steady_mu(B.Sim(_meso(walls=True), precision=B.SDPD_PREC_FP64))
+    assert abs(mu_w / mu_p - 1.0) <= 0.02, (mu_w, mu_p)
