@@ -79,7 +79,8 @@ typedef struct {
     int body_axis, split_axis;
     int pressure_filter, clamp_negative_p, artvis; /* switches (Sections 2.1, 2.5, 4.4) */
     int dem_law;          /* 0: Eqs. deminputA-F as printed; 1: linear kn + restitution */
-    int pad_;
+    int density_reinit;   /* 1: Shepard density reinitialisation at every evaluation (after
+                             Colagrossi & Landrini; text under Algorithm 1), 0: off       */
     unsigned long long seed; /* noise seed                                          */
 } sdpd_params;
 
@@ -168,6 +169,15 @@ sdpd_status sdpd_step(sdpd_ctx *ctx, long long n_steps, void *stream);
  * counter-flowing halves (D = half the box).  Synchronous. */
 sdpd_status sdpd_viscosity_probe(sdpd_ctx *ctx, int inst, int n_bins, double *profile_out,
                                  double *mu_app_out);
+
+/* Viscosity from the curvature of the steady profile (Section 4.1: the
+ * parabola of Eq. poiseuanasol fitted to the convex and concave halves): for
+ * each half of the split axis a least-squares parabola through the slab means
+ * (n_bins slabs as sdpd_viscosity_probe) whose centres lie at least h from
+ * the ends of the half, mu = -+ rho0 g / v''; the mean of the two halves in
+ * *mu_fit_out.  Independent of where a wall's no-slip plane lies.  Needs at
+ * least 4 such slabs per half (else SDPD_E_INVALID).  Synchronous. */
+sdpd_status sdpd_viscosity_fit(sdpd_ctx *ctx, int inst, int n_bins, double *mu_fit_out);
 
 /* Host copies of one instance's state (NULL skips a field): x, v, w, F, N
  * [n][3]; d (number density), p (pressure) [n].  Synchronous. */
@@ -266,7 +276,7 @@ sdpd_status sdpd_noise_normals(int precision, unsigned long long seed, int inst,
  * and fails with SDPD_E_INVALID otherwise.  Both make the next step rebuild
  * the neighbour lists, so a run restored from an image continues bit for bit
  * as the run that wrote it. */
-sdpd_status sdpd_checkpoint_size(const sdpd_ctx *ctx, long long *bytes);
+sdpd_status sdpd_checkpoint_size(sdpd_ctx *ctx, long long *bytes);
 sdpd_status sdpd_checkpoint(sdpd_ctx *ctx, void *buf, long long bytes);
 sdpd_status sdpd_restore(sdpd_ctx *ctx, const void *buf, long long bytes);
 

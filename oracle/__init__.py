@@ -47,7 +47,7 @@ class OrcParams(C.Structure):
         ("periodic", C.c_int * 3),
         ("body_axis", C.c_int), ("split_axis", C.c_int),
         ("pressure_filter", C.c_int), ("clamp_negative_p", C.c_int), ("artvis", C.c_int),
-        ("dem_law", C.c_int), ("pad_", C.c_int),
+        ("dem_law", C.c_int), ("density_reinit", C.c_int),
         ("seed", C.c_uint64),
     ]
 
@@ -106,6 +106,7 @@ def lib():
         L.orc_get_pairs.restype = C.c_long
         L.orc_get_pairs.argtypes = [C.c_void_p, C.c_long, ip]
         L.orc_density.argtypes = [C.c_void_p]
+        L.orc_reinit.argtypes = [C.c_void_p]
         L.orc_filter.argtypes = [C.c_void_p]
         L.orc_forces.argtypes = [C.c_void_p, C.c_int]
         L.orc_update.argtypes = [C.c_void_p, C.c_int]
@@ -132,9 +133,7 @@ def make_params(p: dict) -> OrcParams:
     """Fill the oracle's parameter struct from a case parameter dict."""
     s = OrcParams()
     for name, _ in OrcParams._fields_:
-        if name == "pad_":
-            continue
-        val = p[name]
+        val = p.get(name, 0) if name == "density_reinit" else p[name]
         if name in ("origin", "box", "g"):
             getattr(s, name)[:] = [float(v) for v in val]
         elif name == "periodic":
@@ -301,6 +300,9 @@ class OracleSim:
 
     def density(self):
         lib().orc_density(self._h)
+
+    def reinit(self):
+        lib().orc_reinit(self._h)
 
     def filter(self):
         lib().orc_filter(self._h)

@@ -52,7 +52,7 @@ typedef struct {
     int periodic[3];
     int body_axis, split_axis;        /* forcing direction, splitting direction */
     int pressure_filter, clamp_negative_p, artvis, dem_law;
-    int pad_;
+    int density_reinit;               /* 1: Shepard density reinitialisation (reading B5) */
     uint64_t seed;
 } orc_params;
 
@@ -590,6 +590,43 @@ void orc_density(orc_sim *s)
     }
 }
 
+/* Density reinitialisation (Section 2.1 and the text under Algorithm 1,
+ * after Colagrossi and Landrini 2003).  reading B5: the zeroth-order (Shepard)
+ * form applied to the summation density at every evaluation,
+ *   d~_i = (W(0) + sum_j W_ij) / (W(0)/d_i + sum_j W_ij/d_j),
+ * i.e. the W-weighted harmonic mean of the densities around i; outer-wall
+ * particles keep theirs.  Pressure follows from the EOS again. */
+void orc_reinit(orc_sim *s)
+{
+    const orc_params *P = &s->P;
+    if (!P->density_reinit) return;
+    const double h = P->r_c;
+    const double mf = P->rho0 * P->dx * P->dx * P->dx;
+    double *dn = (double *)malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(double));
+    for (int i = 0; i < s->n; ++i) {
+        if (s->type[i] == T_OUTER_WALL) { dn[i] = s->d[i]; continue; }
+        double w0 = orc_W(0.0, h);
+        double num = w0, den = w0 / s->d[i];
+        for (int k = s->nb_off[i]; k < s->nb_off[i + 1]; ++k) {
+            int j = s->nb[k];
+            double r[3];
+            double r2 = pair_vec(P, s->x + 3 * i, s->x + 3 * j, r);
+            double W = orc_W(sqrt(r2), h);
+            num += W;
+            den += W / s->d[j];
+        }
+        dn[i] = num / den;
+    }
+    for (int i = 0; i < s->n; ++i) {
+        s->d[i] = dn[i];
+        s->rho[i] = mf * dn[i];
+        double pi = orc_eos(s->rho[i], P->rho0, P->p0, P->alpha, P->beta_p);
+        if (P->clamp_negative_p && pi < 0.0) pi = 0.0;
+        s->p[i] = pi;
+    }
+    free(dn);
+}
+
 /* smoothe_particle_pres (Algorithm 1): pressure filter (Imoto 2019).
  * reading: Shepard average over the density neighbour set, self included,
  *   p~_i = (p_i W(0) + sum_j p_j W_ij) / (W(0) + sum_j W_ij);
@@ -1057,6 +1094,7 @@ int orc_substep(orc_sim *s, int velver)
 {
     orc_neighbors(s);
     orc_density(s);
+    orc_reinit(s);
     orc_filter(s);
     orc_forces(s, velver);
     orc_update(s, velver);
@@ -1081,6 +1119,7 @@ int orc_evaluate(orc_sim *s, int velver)
 {
     orc_neighbors(s);
     orc_density(s);
+    orc_reinit(s);
     orc_filter(s);
     orc_forces(s, velver);
     return s->overflow ? 1 : 0;

@@ -44,7 +44,7 @@ class SdpdParams(C.Structure):
         ("periodic", C.c_int * 3),
         ("body_axis", C.c_int), ("split_axis", C.c_int),
         ("pressure_filter", C.c_int), ("clamp_negative_p", C.c_int), ("artvis", C.c_int),
-        ("dem_law", C.c_int), ("pad_", C.c_int),
+        ("dem_law", C.c_int), ("density_reinit", C.c_int),
         ("seed", C.c_ulonglong),
     ]
 
@@ -52,9 +52,7 @@ class SdpdParams(C.Structure):
 def make_params(p: dict) -> SdpdParams:
     s = SdpdParams()
     for name, _ in SdpdParams._fields_:
-        if name == "pad_":
-            continue
-        val = p[name]
+        val = p.get(name, 0) if name == "density_reinit" else p[name]
         if name in ("origin", "box", "g"):
             getattr(s, name)[:] = [float(v) for v in val]
         elif name == "periodic":
@@ -76,7 +74,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
            "sdpd_set_force_mode", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
            "sdpd_check",
-           "sdpd_last_error", "sdpd_noise_normals", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
+           "sdpd_last_error", "sdpd_noise_normals", "sdpd_viscosity_fit", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
            "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
 
 
@@ -126,6 +124,7 @@ def load(build_if_missing: bool = True):
         "sdpd_density_noalloc": (st, [C.POINTER(SdpdParams), C.c_longlong, vp, vp, vp, vp, vp]),
         "sdpd_check": (st, [vp]),
         "sdpd_last_error": (C.c_char_p, []),
+        "sdpd_viscosity_fit": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_double)]),
         "sdpd_checkpoint_size": (st, [vp, C.POINTER(C.c_longlong)]),
         "sdpd_checkpoint": (st, [vp, vp, C.c_longlong]),
         "sdpd_restore": (st, [vp, vp, C.c_longlong]),
@@ -289,6 +288,12 @@ class Sim:
         out = np.zeros(16)
         _check(load().sdpd_diagnostics(self._h, k, _dp(out)))
         return out
+
+    def viscosity_fit(self, k: int = 0, n_bins: int = 32) -> float:
+        """Viscosity from the curvature of the steady profile (sdpd_viscosity_fit)."""
+        mu = C.c_double()
+        _check(load().sdpd_viscosity_fit(self._h, k, n_bins, C.byref(mu)))
+        return mu.value
 
     def checkpoint(self) -> np.ndarray:
         """The dynamic state as a byte image (sdpd_checkpoint)."""

@@ -51,7 +51,7 @@ struct sdpd_ctx {
     std::vector<void *> allocs;        // fixed-size buffers
     std::vector<void *> geo_allocs;    // buffers sized by the grid / rigid count
     Inst *d_inst = nullptr;
-    int any_filter = 0, any_artvis = 0;
+    int any_filter = 0, any_artvis = 0, any_reinit = 0;
     int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct
     double skin = 0.03;                // Verlet skin as a fraction of h
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
@@ -231,6 +231,7 @@ sdpd_status prepare(sdpd_ctx *c)
         for (int a = 0; a < 3; ++a) I.g[a] = p.g[a];
         I.body_amp = p.body_amp; I.body_axis = p.body_axis; I.split_axis = p.split_axis;
         I.filter = p.pressure_filter ? 1 : 0; I.clamp = p.clamp_negative_p ? 1 : 0;
+        I.reinit = p.density_reinit ? 1 : 0;
         I.artvis = p.artvis ? 1 : 0; I.dem_law = p.dem_law;
         I.noise = (p.coeff_t != 0.0 && p.kBT > 0.0) ? 1 : 0;
         I.artvis_rlim = p.artvis_alpha * p.dx; I.artvis_e = p.artvis_e;
@@ -342,9 +343,11 @@ sdpd_status prepare(sdpd_ctx *c)
     CUDA_TRY(cudaMemcpy(c->d_inst, c->inst.data(), sizeof(Inst) * c->n_inst, cudaMemcpyHostToDevice));
     b.inst = c->d_inst;
     c->any_filter = 0;
+    c->any_reinit = 0;
     c->any_artvis = 0;
     for (auto &I : c->inst) {
         c->any_filter |= I.filter;
+        c->any_reinit |= I.reinit;
         c->any_artvis |= I.artvis;
     }
     c->geometry_ready = true;
@@ -473,7 +476,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;
     }
     IALLOC(b.xl64, N); IALLOC(b.dsp, N);
-    IALLOC(b.aclose, N); IALLOC(b.aclose_ok, 1);
+    IALLOC(b.aclose, N); IALLOC(b.aclose_ok, 1); IALLOC(b.sdr, N);
     IALLOC(b.need_build, 1); IALLOC(b.fresh, 1);
     IALLOC(b.list_epoch, 1); IALLOC(b.cache_epoch, 1); IALLOC(b.cache_step, 1);
     {
@@ -639,9 +642,11 @@ long long ckpt_bytes(const sdpd_ctx *c)
 }
 }  // namespace
 
-sdpd_status sdpd_checkpoint_size(const sdpd_ctx *c, long long *bytes)
+sdpd_status sdpd_checkpoint_size(sdpd_ctx *c, long long *bytes)
 {
     if (!c || !bytes) return fail(SDPD_E_INVALID, "sdpd_checkpoint_size: NULL argument");
+    sdpd_status s = ensure_geometry(c);   // the rigid-particle count is known from here on
+    if (s != SDPD_OK) return s;
     *bytes = ckpt_bytes(c);
     return SDPD_OK;
 }
@@ -649,6 +654,8 @@ sdpd_status sdpd_checkpoint_size(const sdpd_ctx *c, long long *bytes)
 sdpd_status sdpd_checkpoint(sdpd_ctx *c, void *buf, long long bytes)
 {
     if (!c || !buf) return fail(SDPD_E_INVALID, "sdpd_checkpoint: NULL argument");
+    sdpd_status g = ensure_geometry(c);
+    if (g != SDPD_OK) return g;
     if (bytes < ckpt_bytes(c)) return fail(SDPD_E_INVALID, "sdpd_checkpoint: buffer too small");
     CUDA_TRY(cudaDeviceSynchronize());
     sdpd_status e = check_err(c);
@@ -683,6 +690,8 @@ sdpd_status sdpd_restore(sdpd_ctx *c, const void *buf, long long bytes)
     std::memcpy(&h, p, sizeof h);
     p += sizeof h;
     if (h.magic != CKPT_MAGIC || h.version != 1u) return fail(SDPD_E_INVALID, "sdpd_restore: not a checkpoint image");
+    sdpd_status g = ensure_geometry(c);   // prepares a fresh context (rigid lists, histories)
+    if (g != SDPD_OK) return g;
     if (h.n != c->N || h.nrigid != c->b.nrigid || h.K != c->K)
         return fail(SDPD_E_INVALID, "sdpd_restore: image of another context shape (particles, spheres, contacts)");
     if (bytes < ckpt_bytes(c)) return fail(SDPD_E_INVALID, "sdpd_restore: image truncated");
@@ -738,7 +747,7 @@ sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
     (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->cells_valid) return fail(SDPD_E_STATE, "sdpd_build_cells must precede sdpd_compute_density");
-    launch_density(c->b, c->precision, c->any_filter, c->newton3, nullptr, (cudaStream_t)stream);
+    launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, nullptr, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     c->density_valid = true;
     return SDPD_OK;
@@ -798,7 +807,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         c->density_valid = false;
     }
     if (!c->density_valid) {
-        launch_density(c->b, c->precision, c->any_filter, c->newton3, nullptr, st);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, nullptr, st);
         c->density_valid = true;
     }
     if (!c->graph) {
@@ -812,12 +821,12 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         // at velver 1 only after such a build, at velver 2 always
         cudaStream_t cs = c->cap_stream;
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter, c->newton3, c->b.fresh, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, c->b.fresh, cs);
         launch_drag(c->b, cs);
         launch_forces(c->b, c->precision, 1, c->newton3, cs);
         launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter, c->newton3, nullptr, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, nullptr, cs);
         launch_drag(c->b, cs);
         launch_forces(c->b, c->precision, 2, c->newton3, cs);
         launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);
@@ -918,6 +927,54 @@ sdpd_status sdpd_viscosity_probe(sdpd_ctx *c, int inst, int n_bins, double *prof
     const double D = 0.5 * p.box[p.split_axis];
     if (mu_app_out) *mu_app_out = p.rho0 * p.body_amp * D * D / (12.0 * V);
     return check_err(c);
+}
+
+sdpd_status sdpd_viscosity_fit(sdpd_ctx *c, int inst, int n_bins, double *mu_fit_out)
+{
+    if (!mu_fit_out) return fail(SDPD_E_INVALID, "sdpd_viscosity_fit: NULL output");
+    std::vector<double> prof(n_bins > 0 ? n_bins : 1);
+    double mu_mean = 0.0;
+    sdpd_status s = sdpd_viscosity_probe(c, inst, n_bins, prof.data(), &mu_mean);
+    if (s != SDPD_OK) return s;
+    const sdpd_params &p = c->hi[inst].P;
+    const int a = p.split_axis;
+    const double L = p.box[a], wb = L / n_bins, h = p.r_c;
+    double mu_sum = 0.0;
+    for (int half = 0; half < 2; ++half) {
+        // least squares v = c0 + c1 t + c2 t^2 over the slabs of this half whose
+        // centres lie at least h from its ends (walls or splitting planes)
+        const double y0 = half * 0.5 * L, y1 = y0 + 0.5 * L, ym = 0.5 * (y0 + y1);
+        double S[5] = { 0, 0, 0, 0, 0 }, T[3] = { 0, 0, 0 };
+        int used = 0;
+        for (int k = 0; k < n_bins; ++k) {
+            const double y = (k + 0.5) * wb;
+            if (y < y0 + h || y > y1 - h) continue;
+            const double t = y - ym, v = prof[k];
+            double tp = 1.0;
+            for (int e = 0; e < 5; ++e) { S[e] += tp; tp *= t; }
+            T[0] += v; T[1] += v * t; T[2] += v * t * t;
+            ++used;
+        }
+        if (used < 4) return fail(SDPD_E_INVALID, "sdpd_viscosity_fit: fewer than 4 slabs h away from the ends of a half");
+        // normal equations [S0 S1 S2; S1 S2 S3; S2 S3 S4] c = T, Cramer's rule for c2
+        const double M[3][3] = { { S[0], S[1], S[2] }, { S[1], S[2], S[3] }, { S[2], S[3], S[4] } };
+        auto det3 = [](const double m[3][3]) {
+            return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                   m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+        };
+        double M2[3][3];
+        for (int r = 0; r < 3; ++r) {
+            M2[r][0] = M[r][0];
+            M2[r][1] = M[r][1];
+            M2[r][2] = T[r];
+        }
+        const double c2 = det3(M2) / det3(M);
+        // steady state: mu v'' = -rho g on the lower half (+g), +rho g above
+        const double g = half == 0 ? p.body_amp : -p.body_amp;
+        mu_sum += -p.rho0 * g / (2.0 * c2);
+    }
+    *mu_fit_out = 0.5 * mu_sum;
+    return SDPD_OK;
 }
 
 sdpd_status sdpd_get_state(sdpd_ctx *c, int inst, double *x, double *v, double *w, double *F, double *N,

@@ -42,7 +42,7 @@ struct Inst {
     double coeff_c, coeff_d, coeff_r, coeff_t;
     double g[3], body_amp;
     int body_axis, split_axis;
-    int filter, clamp, artvis, dem_law, noise;
+    int filter, clamp, artvis, dem_law, noise, reinit;
     double artvis_rlim, artvis_e;
     double kn, kt_ratio, zeta, nu_p, E_p, mu_fric;
     double lub_gap_min, eps_min, Vf;
@@ -81,6 +81,7 @@ struct Bufs {
     double4_32a *A64, *B64, *C64, *D64;
     int *stype;
     double *sd, *sp, *sp2;     // density, pressure (raw / filtered) per slot
+    double *sdr;               // reinitialised density (scratch of the reinitialisation pass)
     // neighbour lists: owned pairs first (Newton-3 ownership), see k_neighbors
     int *nbr, *ncnt, *nfirst;  // nfirst = length of the owned prefix
     int *skey;                 // cell key per slot
@@ -331,7 +332,9 @@ void set_last_error(const char *msg);
 // (defined in k_cells.cu, k_pairs.cu, k_update.cu; all enqueue on `st`)
 // gate: nullptr = always build; else build only when *gate != 0
 void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, cudaStream_t st);
-void launch_density(const Bufs &b, int precision, int any_filter, int newton3, const int *gate, cudaStream_t st);
+// dflags: bit 0 some instance filters the pressure, bit 1 some instance
+// reinitialises the density
+void launch_density(const Bufs &b, int precision, int dflags, int newton3, const int *gate, cudaStream_t st);
 void launch_drag(const Bufs &b, cudaStream_t st);
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st);
 void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st);

@@ -326,6 +326,62 @@ __global__ void __launch_bounds__(256) k_density_gather(Bufs b, int any_filter, 
     }
 }
 
+// ------------------------------------------------------ density reinitialisation
+// Shepard reinitialisation of the summation density (after Colagrossi and
+// Landrini; the text under Algorithm 1): d~_i = (W(0) + sum_j W_ij) /
+// (W(0)/d_i + sum_j W_ij/d_j) over the density neighbours, outer walls keep
+// theirs; the pressure follows from Eq. prtcpres.  The new densities go to
+// sdr (the neighbours' old values are still read) and k_reinit_copy moves
+// them back.
+template <class R>
+__global__ void __launch_bounds__(256) k_reinit(Bufs b, int any_filter, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.N) return;
+    const int gi = b.perm[s];
+    const Inst &I = b.inst[b.pinst[gi]];
+    const double di = b.sd[s];
+    double d = di;
+    if (I.reinit && b.stype[s] != T_OUTER) {
+        const auto *A = Mir<R>::A(b);
+        const auto Ai = A[s];
+        const Geo<R> geo(I);
+        const int n = b.ncnt[s];
+        const long long Np = b.Npad;
+        const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
+        Acc<R> num(I.W0), den(I.W0 / di);
+        for (int k = 0; k < n; ++k) {
+            const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
+            if (e & NB_FAR) continue;
+            R rx, ry, rz, r2;
+            if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
+            const R q = sqrt(r2) * irc;
+            const R om = q < R(1) ? R(1) - q : R(0);
+            const R W = Wc * (R(1) + R(3) * q) * om * om * om;
+            num.add(W);
+            den.add(W / (R)b.sd[e]);
+        }
+        d = num.value() / den.value();
+    }
+    const double rho = I.mf * d;
+    double p = I.p0 * pow(rho / I.rho0, I.alpha) - I.beta_p;
+    if (I.clamp && p < 0.0) p = 0.0;
+    b.sdr[s] = d;
+    if (I.reinit) b.sp[s] = p;
+    if (!any_filter) {
+        b.sp2[s] = b.sp[s];
+        finalize_slot<R>(b, s, d, b.sp[s]);
+    }
+}
+
+__global__ void k_reinit_copy(Bufs b, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < b.N) b.sd[s] = b.sdr[s];
+}
+
 // ------------------------------------------------------------ pressure filter
 template <class R>
 __global__ void __launch_bounds__(256) k_filter(Bufs b, const int *gate)
@@ -1157,19 +1213,34 @@ static unsigned persistent_grid(K kernel, int block, long long N)
     return (unsigned)std::min<long long>(need, (long long)nsm * per_sm);
 }
 
-void launch_density(const Bufs &b, int precision, int any_filter, int newton3, const int *gate, cudaStream_t st)
+void launch_density(const Bufs &b, int precision, int dflags, int newton3, const int *gate, cudaStream_t st)
 {
     if (!b.N) return;
+    const int any_filter = dflags & 1, any_reinit = (dflags >> 1) & 1;
+    // the density kernels leave the mirrors to a later pass when one follows
+    const int defer = any_filter | any_reinit;
     if (precision == SDPD_PREC_FP64 && newton3) {
         cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
         k_density_half<<<persistent_grid(k_density_half, b.pair_block, b.N), b.pair_block, 0, st>>>(b, gate);
-        k_density_gather<<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+        k_density_gather<<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
+        if (any_reinit) {
+            k_reinit<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+            k_reinit_copy<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
+        }
         if (any_filter) k_filter<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     } else if (precision == SDPD_PREC_SPLIT) {
-        k_density<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+        k_density<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
+        if (any_reinit) {
+            k_reinit<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+            k_reinit_copy<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
+        }
         if (any_filter) k_filter<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     } else {
-        k_density<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+        k_density<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
+        if (any_reinit) {
+            k_reinit<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
+            k_reinit_copy<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
+        }
         if (any_filter) k_filter<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     }
 }

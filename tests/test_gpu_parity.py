@@ -323,3 +323,22 @@ def test_newton3_equals_direct(name, precision):
     assert rel_l2(sa["N"], sb["N"]) < tol
     orc = _oracle_eval(case, step=4)
     assert rel_l2(sb["F"], orc.state()["F"]) < TOL_FORCE[precision]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("name", ["periodic12", "dambreak_small"])
+def test_density_reinit_matches_oracle(name, precision):
+    # reading B5: Shepard reinitialisation of the summation density before
+    # the pressure filter; densities, pressures and forces against the oracle
+    case = dict(CASES[name])
+    case["params"] = dict(case["params"], density_reinit=1)
+    orc = _oracle_eval(case, step=2)
+    sim = _gpu_eval(case, precision, step=2)
+    so, sg = orc.state(), sim.state()
+    tol_d = 1e-12 if precision == B.SDPD_PREC_FP64 else 1e-6
+    assert rel_l2(sg["d"], so["d"]) < tol_d
+    # the reinitialisation changed something on the free surface
+    base = _oracle_eval(CASES[name], step=2).state()["d"]
+    if name == "dambreak_small":
+        assert rel_l2(so["d"], base) > 1e-6
+    assert rel_l2(sg["F"], so["F"]) < TOL_FORCE[precision]

@@ -65,10 +65,21 @@ def test_batched_viscometers_agree_with_single_runs():
     assert np.all(np.diff(mus_b) > 0)
 
 
+def _steady_fit(sim, k=0, steps=900, avg=300, every=10, n_bins=32):
+    sim.step(steps - avg)
+    mus = []
+    for _ in range(avg // every):
+        sim.step(every)
+        mus.append(sim.viscosity_fit(k, n_bins))
+    return float(np.mean(mus))
+
+
 def test_wall_periodic_hybrid_agrees_with_fully_periodic():
     # Section 4.1: with dummy-particle walls on the split axis and periodic x,
-    # z, the viscosity read-out differs from the fully periodic one by at most
-    # 2 % (the paper's statement)
-    mu_p = _steady_mu(B.Sim(_meso(), precision=B.SDPD_PREC_FP64))
-    mu_w = _steady_mu(B.Sim(_meso(walls=True), precision=B.SDPD_PREC_FP64))
+    # z, the viscosity from the fitted profiles differs from the fully
+    # periodic one by at most 2 % (the paper's statement).  The curvature fit
+    # does not depend on where the walls' no-slip plane lies.
+    mu_p = _steady_fit(B.Sim(_meso(), precision=B.SDPD_PREC_FP64))
+    mu_w = _steady_fit(B.Sim(_meso(walls=True), precision=B.SDPD_PREC_FP64))
+    assert mu_p == pytest.approx(25.0, rel=0.05), mu_p
     assert abs(mu_w / mu_p - 1.0) <= 0.02, (mu_w, mu_p)
