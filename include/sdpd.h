@@ -108,7 +108,10 @@ sdpd_status sdpd_set_particles(sdpd_ctx *ctx, int inst, long long n, const doubl
 
 /* Upload positions, velocities and spins of all instances at once ([N][3],
  * N = sum of n_particles; any pointer may be NULL to keep that field).
- * Asynchronous on `stream` (host memory should be pinned). */
+ * Asynchronous on `stream` (host memory should be pinned).  When the context
+ * has current neighbour lists they are kept: the particles move by their
+ * displacement and the next step rebuilds only if one moved more than half
+ * the Verlet skin since the last build (results do not depend on it). */
 sdpd_status sdpd_upload_state(sdpd_ctx *ctx, const double *x, const double *v, const double *w,
                               void *stream);
 

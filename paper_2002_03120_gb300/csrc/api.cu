@@ -476,7 +476,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;
     }
     IALLOC(b.xl64, N); IALLOC(b.dsp, N);
-    IALLOC(b.aclose, N); IALLOC(b.aclose_ok, 1); IALLOC(b.sdr, N);
+    IALLOC(b.aclose, N); IALLOC(b.aclose_ok, 1); IALLOC(b.sdr, N); IALLOC(b.xs, 3 * N);
     IALLOC(b.need_build, 1); IALLOC(b.fresh, 1);
     IALLOC(b.list_epoch, 1); IALLOC(b.cache_epoch, 1); IALLOC(b.cache_step, 1);
     {
@@ -607,6 +607,19 @@ sdpd_status sdpd_upload_state(sdpd_ctx *c, const double *x, const double *v, con
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
+    (void)cudaGetLastError();
+    if (c->cells_valid) {
+        // keep the lists: move the particles by their displacement and let
+        // the gated build of the next step decide (half the skin)
+        if (x) CUDA_TRY(cudaMemcpyAsync(c->b.xs, x, bytes, cudaMemcpyDefault, st));
+        if (v) CUDA_TRY(cudaMemcpyAsync(c->b.v, v, bytes, cudaMemcpyDefault, st));
+        if (w) CUDA_TRY(cudaMemcpyAsync(c->b.w, w, bytes, cudaMemcpyDefault, st));
+        launch_absorb(c->b, c->precision, c->b.xs, x ? 1 : 0, st);
+        CUDA_TRY(cudaGetLastError());
+        if (x) c->density_valid = false;
+        c->drag_valid = false;
+        return SDPD_OK;
+    }
     if (x) CUDA_TRY(cudaMemcpyAsync(c->b.x, x, bytes, cudaMemcpyDefault, st));
     if (v) CUDA_TRY(cudaMemcpyAsync(c->b.v, v, bytes, cudaMemcpyDefault, st));
     if (w) CUDA_TRY(cudaMemcpyAsync(c->b.w, w, bytes, cudaMemcpyDefault, st));

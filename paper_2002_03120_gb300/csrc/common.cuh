@@ -82,6 +82,7 @@ struct Bufs {
     int *stype;
     double *sd, *sp, *sp2;     // density, pressure (raw / filtered) per slot
     double *sdr;               // reinitialised density (scratch of the reinitialisation pass)
+    double *xs;                // [N][3] staging of uploaded positions
     // neighbour lists: owned pairs first (Newton-3 ownership), see k_neighbors
     int *nbr, *ncnt, *nfirst;  // nfirst = length of the owned prefix
     int *skey;                 // cell key per slot
@@ -343,6 +344,7 @@ void launch_step_done(const Bufs &b, cudaStream_t st);
 void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long n);
 void launch_diag(const Bufs &b, int inst, cudaStream_t st, long long n);
 void launch_count_pairs(const Bufs &b, cudaStream_t st);
+void launch_absorb(const Bufs &b, int precision, const double *xs, int has_x, cudaStream_t st);
 void launch_noise_normals(int precision, long long n, const uint32_t *gi, const uint32_t *gj, uint32_t step,
                           uint32_t k0, uint32_t k1, double *out, cudaStream_t st);
 

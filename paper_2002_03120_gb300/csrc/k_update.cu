@@ -29,10 +29,6 @@ __device__ __forceinline__ void write_vel_mirror(const Bufs &b, long long s, con
     C[s] = Cs;
 }
 
-// Velocity Verlet (Eqs. newton1, newton2): v += dt/2 F/m, w += dt/2 N/I;
-// velver 1 also drifts x += dt v, wraps periodic axes and mirrors particles
-// that crossed a wall plane (normal velocity reversed).  The arithmetic is
-// written without fused multiply-adds so it repeats the oracle bit for bit.
 // a / d rounded to nearest from y = RN(1/d) by Markstein's method (P.
 // Markstein, IBM J. Res. Dev. 34, 1990): q0 = RN(a y), the remainder
 // r = a - d q0 is exact with a fused multiply-add, and RN(q0 + r y) is the
@@ -45,6 +41,10 @@ __device__ __forceinline__ double div_rn(double a, double d, double y)
     return __fma_rn(r, y, q0);
 }
 
+// Velocity Verlet (Eqs. newton1, newton2): v += dt/2 F/m, w += dt/2 N/I;
+// velver 1 also drifts x += dt v, wraps periodic axes and mirrors particles
+// that crossed a wall plane (normal velocity reversed).  The arithmetic is
+// written without fused multiply-adds so it repeats the oracle bit for bit.
 template <class R>
 __global__ void k_integrate(Bufs b, int velver)
 {
@@ -114,6 +114,54 @@ __global__ void k_integrate(Bufs b, int velver)
     }
     if (bad) atomicOr(b.err, ERR_NONFINITE);
     write_vel_mirror<R>(b, s, v, w);
+}
+
+// Absorb uploaded state (sdpd_upload_state) into a context whose lists are
+// valid: each particle moves by its displacement (minimum image on periodic
+// axes), the cell-relative mirrors and the displacement since the build move
+// with it, and the velocity mirrors take the uploaded velocities.  A
+// displacement beyond half the skin requests a rebuild (the gated build of
+// the next step), exactly as after a drift; otherwise the lists still hold
+// every pair within h.
+template <class R>
+__global__ void k_absorb(Bufs b, const double *__restrict__ xs, int has_x)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.N) return;
+    const int g = b.perm[s];
+    const Inst &I = b.inst[b.pinst[g]];
+    if (has_x) {
+        double dl[3], x[3];
+        for (int a = 0; a < 3; ++a) {
+            const double x0 = b.x[3 * g + a], xa = xs[3 * g + a];
+            double d = xa - x0;
+            if (I.periodic[a]) {
+                if (d > 0.5 * I.box[a]) d -= I.box[a];
+                else if (d < -0.5 * I.box[a]) d += I.box[a];
+            }
+            dl[a] = d;
+            x[a] = xa;
+            b.x[3 * g + a] = xa;
+        }
+        double4_32a xl = b.xl64[s], ds = b.dsp[s];
+        xl.x += dl[0]; xl.y += dl[1]; xl.z += dl[2];
+        ds.x += dl[0]; ds.y += dl[1]; ds.z += dl[2];
+        b.xl64[s] = xl;
+        b.dsp[s] = ds;
+        float4 a32 = b.A32[s];
+        a32.x = (float)xl.x; a32.y = (float)xl.y; a32.z = (float)xl.z;
+        b.A32[s] = a32;
+        if (b.A64) {
+            double4_32a a64 = b.A64[s];
+            a64.x = x[0]; a64.y = x[1]; a64.z = x[2];
+            b.A64[s] = a64;
+        }
+        if (ds.x * ds.x + ds.y * ds.y + ds.z * ds.z > I.half_skin * I.half_skin) *b.need_build = 1;
+    }
+    const double v[3] = { b.v[3 * g], b.v[3 * g + 1], b.v[3 * g + 2] };
+    const double w[3] = { b.w[3 * g], b.w[3 * g + 1], b.w[3 * g + 2] };
+    write_vel_mirror<R>(b, s, v, w);
+    if (s == 0) *b.aclose_ok = 0;   // positions changed
 }
 
 // Collision-method artificial viscosity: pairs of mobile particles closer
@@ -351,6 +399,13 @@ void launch_noise_normals(int precision, long long n, const uint32_t *gi, const 
         k_noise_normals<double><<<nblk(n, 256), 256, 0, st>>>(n, gi, gj, step, k0, k1, out);
     else
         k_noise_normals<float><<<nblk(n, 256), 256, 0, st>>>(n, gi, gj, step, k0, k1, out);
+}
+
+void launch_absorb(const Bufs &b, int precision, const double *xs, int has_x, cudaStream_t st)
+{
+    if (!b.N) return;
+    if (precision == SDPD_PREC_SPLIT) k_absorb<float><<<nblk(b.N, 256), 256, 0, st>>>(b, xs, has_x);
+    else k_absorb<double><<<nblk(b.N, 256), 256, 0, st>>>(b, xs, has_x);
 }
 
 void launch_count_pairs(const Bufs &b, cudaStream_t st)
