@@ -175,9 +175,10 @@ sdpd_status sdpd_viscosity_probe(sdpd_ctx *ctx, int inst, int n_bins, double *pr
 
 /* Viscosity from the curvature of the steady profile (Section 4.1: the
  * parabola of Eq. poiseuanasol fitted to the convex and concave halves): for
- * each half of the split axis a least-squares parabola through the slab means
- * (n_bins slabs as sdpd_viscosity_probe) whose centres lie at least h from
- * the ends of the half, mu = -+ rho0 g / v''; the mean of the two halves in
+ * each half of the split axis a least-squares parabola through the slab mean
+ * velocities at the slabs' mean particle positions (n_bins slabs as
+ * sdpd_viscosity_probe), over the slabs at least h from the ends of the
+ * half, mu = -+ rho0 g / v''; the mean of the two halves in
  * *mu_fit_out.  Independent of where a wall's no-slip plane lies.  Needs at
  * least 4 such slabs per half (else SDPD_E_INVALID).  Synchronous. */
 sdpd_status sdpd_viscosity_fit(sdpd_ctx *ctx, int inst, int n_bins, double *mu_fit_out);

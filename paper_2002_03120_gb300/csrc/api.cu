@@ -52,6 +52,7 @@ struct sdpd_ctx {
     std::vector<void *> geo_allocs;    // buffers sized by the grid / rigid count
     Inst *d_inst = nullptr;
     int any_filter = 0, any_artvis = 0, any_reinit = 0;
+    std::vector<double> probe_y;   // mean slab positions of the last viscosity probe
     int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct
     double skin = 0.03;                // Verlet skin as a fraction of h
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
@@ -488,7 +489,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     }
     b.use_cache = 1;
     IALLOC(b.step, 1); IALLOC(b.err, 1); IALLOC(b.pair_count, 1); IALLOC(b.work, 1);
-    IALLOC(b.probe, 4096 * 2 + 64);
+    IALLOC(b.probe, 4096 * 3 + 64);
 #undef IALLOC
     if (cudaMemset(b.need_build, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.fresh, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b.aclose_ok, 0, sizeof(int)) != cudaSuccess ||
@@ -930,10 +931,14 @@ sdpd_status sdpd_viscosity_probe(sdpd_ctx *c, int inst, int n_bins, double *prof
     if (s != SDPD_OK) return s;
     CUDA_TRY(cudaDeviceSynchronize());
     launch_probe(c->b, inst, n_bins, 0, c->hi[inst].n);
-    std::vector<double> h(2 * n_bins + 4);
+    std::vector<double> h(3 * n_bins + 4);
     CUDA_TRY(cudaMemcpy(h.data(), c->b.probe, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
     for (int k = 0; k < n_bins; ++k)
         if (profile_out) profile_out[k] = h[n_bins + k] > 0 ? h[k] / h[n_bins + k] : 0.0;
+    // mean position of each slab's particles (for sdpd_viscosity_fit)
+    c->probe_y.assign(n_bins, -1.0);
+    for (int k = 0; k < n_bins; ++k)
+        if (h[n_bins + k] > 0) c->probe_y[k] = h[2 * n_bins + 4 + k] / h[n_bins + k];
     const sdpd_params &p = c->hi[inst].P;
     const double V = 0.5 * (h[2 * n_bins] / std::max(h[2 * n_bins + 2], 1.0) +
                             h[2 * n_bins + 1] / std::max(h[2 * n_bins + 3], 1.0));
@@ -951,7 +956,7 @@ sdpd_status sdpd_viscosity_fit(sdpd_ctx *c, int inst, int n_bins, double *mu_fit
     if (s != SDPD_OK) return s;
     const sdpd_params &p = c->hi[inst].P;
     const int a = p.split_axis;
-    const double L = p.box[a], wb = L / n_bins, h = p.r_c;
+    const double L = p.box[a], h = p.r_c;
     double mu_sum = 0.0;
     for (int half = 0; half < 2; ++half) {
         // least squares v = c0 + c1 t + c2 t^2 over the slabs of this half whose
@@ -960,8 +965,8 @@ sdpd_status sdpd_viscosity_fit(sdpd_ctx *c, int inst, int n_bins, double *mu_fit
         double S[5] = { 0, 0, 0, 0, 0 }, T[3] = { 0, 0, 0 };
         int used = 0;
         for (int k = 0; k < n_bins; ++k) {
-            const double y = (k + 0.5) * wb;
-            if (y < y0 + h || y > y1 - h) continue;
+            const double y = c->probe_y[k];   // mean position of the slab's particles
+            if (y < 0.0 || y < y0 + h || y > y1 - h) continue;
             const double t = y - ym, v = prof[k];
             double tp = 1.0;
             for (int e = 0; e < 5; ++e) { S[e] += tp; tp *= t; }

@@ -265,6 +265,7 @@ __global__ void k_probe(Bufs b, int inst, int nb)
     const int half = (rel < 0.5 * I.box[ax]) ? 0 : 1;
     atomicAdd(&b.probe[2 * nb + half], half == 0 ? u : -u);
     atomicAdd(&b.probe[2 * nb + 2 + half], 1.0);
+    atomicAdd(&b.probe[2 * nb + 4 + bin], rel);   // mean position of the slab's particles
 }
 
 // diagnostics layout in probe: [0..2] momentum, [3] sum m v^2, [4] sum m,
@@ -359,7 +360,7 @@ void launch_step_done(const Bufs &b, cudaStream_t st) { k_step_done<<<1, 1, 0, s
 
 void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long n)
 {
-    cudaMemsetAsync(b.probe, 0, sizeof(double) * (2 * nbins + 4), st);
+    cudaMemsetAsync(b.probe, 0, sizeof(double) * (3 * nbins + 4), st);
     if (n) k_probe<<<nblk(n, 256), 256, 0, st>>>(b, inst, nbins);
 }
 

@@ -95,14 +95,20 @@ def simulate(pts, seed: int = 0, n: int = 12, steps: int = 1500, avg: int = 500,
              n_bins: int = 24) -> np.ndarray:
     """Apparent viscosity of every sweep point: run `steps` steps, average the
     probe over the last `avg` (one read-out every `every` steps).  Points run
-    as batches of `batch` instances, one engine (one graph) per batch.
-    Non-finite or non-positive read-outs come back as NaN."""
+    as batches of `batch` instances, one engine (one graph) per batch, with
+    the autotuner's setting for the batch shape.  Non-finite or non-positive
+    read-outs come back as NaN."""
+    from . import autotune
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
     mu = np.full(len(pts), np.nan)
     for b0 in range(0, len(pts), batch):
         chunk = pts[b0:b0 + batch]
         insts = [instance(pt, seed + b0 + k, n=n, kbt_scale=kbt_scale) for k, pt in enumerate(chunk)]
+        # force variant, skin and block size for this batch shape (cached
+        # after the first measurement of the size class)
+        setting = autotune.tune(insts, precision=precision)
         sim = B.Sim(insts, precision=precision)
+        autotune.apply(sim, setting)
         sim.step(steps - avg)
         acc = np.zeros(len(chunk))
         reads = 0

@@ -70,4 +70,5 @@ def test_moved_particles_step_like_the_oracle(precision, tol, move):
     orc.run(1)
     o = orc.state()
     assert rel_l2(g["v"][mob], o["v"][mob]) < tol
-    assert rel_l2(g["x"], o["x"]) < 1e-12
+    # positions move by dt v: the velocity difference, scaled by dt / |x|
+    assert rel_l2(g["x"], o["x"]) < (1e-12 if precision == B.SDPD_PREC_FP64 else 1e-9)
