@@ -238,6 +238,7 @@ struct Net {
     float *M, *V;        // Adam moments
     __nv_bfloat16 *Wb;   // BF16 copies of W1..W3 [3][128][128]
     float *Z, *H0, *D;   // training scratch: Z [4][Bmax][128], first-layer input copy, dz buffers
+    float *Gp, *Lp;      // per-tile gradient shares [Bmax/128][NPARAM] and squared-error sums
     float *Y, *DY, *loss;
     int *err;
     int bmax;
@@ -404,9 +405,13 @@ __global__ void __launch_bounds__(128 * NWG, 1) k_mlp_forward(const float *__res
 }
 
 // ------------------------------------------------------------- training
-// One launch = forward + backward of one batch (<= bmax rows, tiles of 128)
-// on one CTA; gradients into G, loss into *loss.  Scratch Z holds the
-// pre-activations of the four hidden layers, D the back-propagated dz.
+// One CTA per 128-row tile of the batch: forward (pre-activations kept in Z),
+// backward through every layer for the tile's rows, the tile's share of each
+// gradient into its row of Gp [ntile][NPARAM] and its squared-error sum into
+// Lp[tile]; k_mlp_reduce adds the tiles in a fixed order.  The output
+// gradient dy = 2 (y - t) / B needs no sum across tiles, so the tiles are
+// independent.  Thread t owns batch row tile * 128 + t (TMEM lane t) in the
+// row-wise steps and output unit t in the column-wise sums.
 __global__ void __launch_bounds__(128, 1) k_mlp_grad(Net net, const float *__restrict__ X,
                                                      const float *__restrict__ T, int B)
 {
@@ -417,11 +422,17 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad(Net net, const float *__res
     uint8_t *sD = smem + 3 * TILE_BYTES;      // second B
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 4 * TILE_BYTES);
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 4 * TILE_BYTES + 16);
+    float *red = reinterpret_cast<float *>(smem + 4 * TILE_BYTES + 32);   // 4 floats
     const int t = threadIdx.x;
-    const int ntile = (B + WID - 1) / WID;
+    const int tile = blockIdx.x;
+    const int r0 = tile * WID;                // first batch row of the tile
+    const int nrow = min(WID, B - r0);        // rows of this tile
+    const int row = r0 + t;
+    const bool valid = t < nrow;
     const int bm = net.bmax;
     float *Z = net.Z;                         // [4][bmax][128]
-    float *G = net.G;
+    float *Dc = net.D, *Dn = net.D + (size_t)bm * WID;   // dz of the current / next layer
+    float *Gp = net.Gp + (size_t)tile * NPARAM;
     const float *P = net.P;
     if (t == 0) mbar_init(mbar);
     if (t < 32) tc_alloc(slot, 256);
@@ -432,157 +443,149 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad(Net net, const float *__res
     uint32_t parity = 0;
     bool ok = true;
     float v[16];
-    // ---------------- forward, storing pre-activations
-    for (int tile = 0; tile < ntile && ok; ++tile) {
-        const int row = tile * WID + t;
-        const bool valid = row < B;
-        const float x0 = valid ? X[3 * row] : 0.f, x1 = valid ? X[3 * row + 1] : 0.f,
-                    x2 = valid ? X[3 * row + 2] : 0.f;
-        for (int c = 0; c < 16; ++c) {
-            float h[8];
+    // ---------------- forward, keeping the pre-activations
+    const float x0 = valid ? X[3 * row] : 0.f, x1 = valid ? X[3 * row + 1] : 0.f, x2 = valid ? X[3 * row + 2] : 0.f;
+    for (int c = 0; c < 16; ++c) {
+        float h[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int o = 8 * c + i;
-                const float z = P[OFF_W0 + 3 * o] * x0 + P[OFF_W0 + 3 * o + 1] * x1 + P[OFF_W0 + 3 * o + 2] * x2 +
-                                P[OFF_B0 + o];
-                Z[(0 * bm + row) * WID + o] = valid ? z : 0.f;
-                h[i] = valid ? gelu(z) : 0.f;
-            }
-            put8(sA, t, 8 * c, h);
+        for (int i = 0; i < 8; ++i) {
+            const int o = 8 * c + i;
+            const float z = P[OFF_W0 + 3 * o] * x0 + P[OFF_W0 + 3 * o + 1] * x1 + P[OFF_W0 + 3 * o + 2] * x2 +
+                            P[OFF_B0 + o];
+            Z[(0 * bm + row) * WID + o] = valid ? z : 0.f;
+            h[i] = valid ? gelu(z) : 0.f;
         }
-        float y = 0.f;
-        for (int l = 1; l <= 3 && ok; ++l) {
-            stage_weights(sB, net.Wb + (l - 1) * WID * WID, false);
-            ok = gemm_128(sA, sB, taddr, false, mbar, parity, net.err);
-            if (!ok) break;
-            for (int c = 0; c < 8; ++c) {
-                acc_row16(taddr, c, v);
+        put8(sA, t, 8 * c, h);
+    }
+    float y = 0.f;
+    for (int l = 1; l <= 3 && ok; ++l) {
+        stage_weights(sB, net.Wb + (l - 1) * WID * WID, false);
+        ok = gemm_128(sA, sB, taddr, false, mbar, parity, net.err);
+        if (!ok) break;
+        for (int c = 0; c < 8; ++c) {
+            acc_row16(taddr, c, v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int o = 16 * c + i;
-                    const float z = v[i] + P[off_b(l) + o];
-                    Z[(l * bm + row) * WID + o] = valid ? z : 0.f;
-                    const float h = valid ? gelu(z) : 0.f;
-                    if (l < 3) v[i] = h;
-                    else y += h * P[OFF_W4 + o];
-                }
-                if (l < 3) {
-                    put8(sA, t, 16 * c, v);
-                    put8(sA, t, 16 * c + 8, v + 8);
-                }
+            for (int i = 0; i < 16; ++i) {
+                const int o = 16 * c + i;
+                const float z = v[i] + P[off_b(l) + o];
+                Z[(l * bm + row) * WID + o] = valid ? z : 0.f;
+                const float h = valid ? gelu(z) : 0.f;
+                if (l < 3) v[i] = h;
+                else y += h * P[OFF_W4 + o];
             }
-            tc_fence_before();
-            __syncthreads();
+            if (l < 3) {
+                put8(sA, t, 16 * c, v);
+                put8(sA, t, 16 * c + 8, v + 8);
+            }
         }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok) goto done;
+    {
+        float dy = 0.f, sq = 0.f;
         if (valid) {
             y += P[OFF_B4];
             net.Y[row] = y;
-            net.DY[row] = 2.0f * (y - T[row]) / (float)B;
+            dy = 2.0f * (y - T[row]) / (float)B;
+            sq = (y - T[row]) * (y - T[row]);
         }
-    }
-    __syncthreads();
-    if (!ok) goto done;
-    // ---------------- output layer gradients and dz of the last hidden layer
-    if (t == 0) {
-        float l = 0.f, gb = 0.f;
-        for (int r = 0; r < B; ++r) {
-            const float d = net.Y[r] - T[r];
-            l += d * d;
-            gb += net.DY[r];
+        net.DY[row] = dy;   // 0 on the rows past B (the scratch holds whole tiles)
+        // the tile's squared-error sum, fixed order: warps, then warps 0..3
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if ((t & 31) == 0) red[t >> 5] = sq;
+        __syncthreads();
+        if (t == 0) net.Lp[tile] = (red[0] + red[1]) + (red[2] + red[3]);
+        // output layer (thread t = unit o): gW4 = sum_rows dy gelu(z3), gb4 = sum_rows dy
+        float gw = 0.f, gb = 0.f;
+        for (int r = 0; r < nrow; ++r) {
+            const float d = net.DY[r0 + r];
+            gw += d * gelu(Z[(3 * bm + r0 + r) * WID + t]);
+            gb += d;
         }
-        *net.loss = l / (float)B;
-        G[OFF_B4] = gb;
-    }
-    {
-        float gw = 0.f;
-        for (int r = 0; r < B; ++r) gw += net.DY[r] * gelu(Z[(3 * bm + r) * WID + t]);
-        G[OFF_W4 + t] = gw;
-    }
-    for (int tile = 0; tile < ntile; ++tile) {
-        const int row = tile * WID + t;
-        if (row < B)
-            for (int o = 0; o < WID; ++o)
-                net.D[row * WID + o] = net.DY[row] * P[OFF_W4 + o] * gelu_prime(Z[(3 * bm + row) * WID + o]);
+        Gp[OFF_W4 + t] = gw;
+        if (t == 0) Gp[OFF_B4] = gb;
+        // dz of the last hidden layer for this thread's row
+        for (int o = 0; o < WID; ++o)
+            Dc[row * WID + o] = valid ? dy * P[OFF_W4 + o] * gelu_prime(Z[(3 * bm + row) * WID + o]) : 0.f;
     }
     __syncthreads();
     // ---------------- hidden layers l = 3, 2, 1 (z_l = W_l a_{l-1} + b_l)
     for (int l = 3; l >= 1 && ok; --l) {
-        // weight gradient: gW_l = dz_l^T a_{l-1}, accumulated over the tiles
-        for (int tile = 0; tile < ntile && ok; ++tile) {
-            const int row = tile * WID + t;
-            const bool valid = row < B;
-            // sC: A = dz^T (rows = out o, K = batch row); sD: B = a^T (rows = in i, K = batch row)
-            for (int o = 0; o < WID; ++o) {
-                put1(sC, o, t, valid ? net.D[row * WID + o] : 0.f);
-                put1(sD, o, t, valid ? gelu(Z[((l - 1) * bm + row) * WID + o]) : 0.f);
-            }
-            ok = gemm_128(sC, sD, taddr + 128, tile > 0, mbar, parity, net.err);
+        // weight gradient over the tile: A = dz^T (rows = unit o, K = row), B = a^T (rows = input i, K = row)
+        for (int o = 0; o < WID; ++o) {
+            put1(sC, o, t, Dc[row * WID + o]);
+            put1(sD, o, t, valid ? gelu(Z[((l - 1) * bm + row) * WID + o]) : 0.f);
         }
+        ok = gemm_128(sC, sD, taddr + 128, false, mbar, parity, net.err);
         if (!ok) break;
         for (int c = 0; c < 8; ++c) {
             acc_row16(taddr + 128, c, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) G[off_W(l) + t * WID + 16 * c + i] = v[i];
+            for (int i = 0; i < 16; ++i) Gp[off_W(l) + t * WID + 16 * c + i] = v[i];
         }
         {
             float gb = 0.f;
-            for (int r = 0; r < B; ++r) gb += net.D[r * WID + t];
-            G[off_b(l) + t] = gb;
+            for (int r = 0; r < nrow; ++r) gb += Dc[(r0 + r) * WID + t];
+            Gp[off_b(l) + t] = gb;
         }
         tc_fence_before();
         __syncthreads();
-        // input gradient: dh = dz_l W_l (A = dz rows, B = W_l^T), dz_{l-1} = dh * gelu'(z_{l-1})
+        // input gradient: dh = dz W_l (A = dz rows, B = W_l^T), dz_{l-1} = dh gelu'(z_{l-1})
         stage_weights(sB, net.Wb + (l - 1) * WID * WID, true);
-        for (int tile = 0; tile < ntile && ok; ++tile) {
-            const int row = tile * WID + t;
-            const bool valid = row < B;
-            for (int c = 0; c < 16; ++c) {
-                float d8[8];
+        for (int c = 0; c < 16; ++c) put8(sA, t, 8 * c, Dc + row * WID + 8 * c);
+        ok = gemm_128(sA, sB, taddr, false, mbar, parity, net.err);
+        if (!ok) break;
+        for (int c = 0; c < 8; ++c) {
+            acc_row16(taddr, c, v);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) d8[i] = valid ? net.D[row * WID + 8 * c + i] : 0.f;
-                put8(sA, t, 8 * c, d8);
+            for (int i = 0; i < 16; ++i) {
+                const int o = 16 * c + i;
+                Dn[row * WID + o] = valid ? v[i] * gelu_prime(Z[((l - 1) * bm + row) * WID + o]) : 0.f;
             }
-            ok = gemm_128(sA, sB, taddr, false, mbar, parity, net.err);
-            if (!ok) break;
-            for (int c = 0; c < 8; ++c) {
-                acc_row16(taddr, c, v);
-                if (valid)
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int o = 16 * c + i;
-                        net.D[(bm + row) * WID + o] = v[i] * gelu_prime(Z[((l - 1) * bm + row) * WID + o]);
-                    }
-            }
-            tc_fence_before();
-            __syncthreads();
         }
-        // the new dz replaces the old
-        for (int tile = 0; tile < ntile; ++tile) {
-            const int row = tile * WID + t;
-            if (row < B)
-                for (int o = 0; o < WID; ++o) net.D[row * WID + o] = net.D[(bm + row) * WID + o];
-        }
+        tc_fence_before();
         __syncthreads();
+        float *tmp = Dc;
+        Dc = Dn;
+        Dn = tmp;
     }
     if (ok) {
-        // input layer: gW0 = dz_0^T x, gb0 = sum dz_0 (thread t = output o)
+        // input layer (thread t = unit o): gW0 = dz_0^T x, gb0 = sum dz_0
         float g0 = 0.f, g1 = 0.f, g2 = 0.f, gb = 0.f;
-        for (int r = 0; r < B; ++r) {
-            const float d = net.D[r * WID + t];
-            g0 += d * X[3 * r];
-            g1 += d * X[3 * r + 1];
-            g2 += d * X[3 * r + 2];
+        for (int r = 0; r < nrow; ++r) {
+            const float d = Dc[(r0 + r) * WID + t];
+            g0 += d * X[3 * (r0 + r)];
+            g1 += d * X[3 * (r0 + r) + 1];
+            g2 += d * X[3 * (r0 + r) + 2];
             gb += d;
         }
-        G[OFF_W0 + 3 * t] = g0;
-        G[OFF_W0 + 3 * t + 1] = g1;
-        G[OFF_W0 + 3 * t + 2] = g2;
-        G[OFF_B0 + t] = gb;
+        Gp[OFF_W0 + 3 * t] = g0;
+        Gp[OFF_W0 + 3 * t + 1] = g1;
+        Gp[OFF_W0 + 3 * t + 2] = g2;
+        Gp[OFF_B0 + t] = gb;
     }
 done:
     tc_fence_before();
     __syncthreads();
     if (t < 32) tc_dealloc(taddr, 256);
+}
+
+// Gradient and loss of the batch: the tiles' shares added in tile order.
+__global__ void k_mlp_reduce(Net net, int ntile, int B)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < NPARAM) {
+        float g = 0.f;
+        for (int i = 0; i < ntile; ++i) g += net.Gp[(size_t)i * NPARAM + k];
+        net.G[k] = g;
+    }
+    if (k == 0) {
+        float l = 0.f;
+        for (int i = 0; i < ntile; ++i) l += net.Lp[i];
+        *net.loss = l / (float)B;
+    }
 }
 
 // Adam (Kingma & Ba) on the FP32 masters; refreshes the BF16 copies.
@@ -655,6 +658,7 @@ sdpd_status mlp_init(int in, int width, int depth, unsigned long long seed, int 
     bool ok = A((void **)&n.P, NPARAM * 4) && A((void **)&n.G, NPARAM * 4) && A((void **)&n.M, NPARAM * 4) &&
               A((void **)&n.V, NPARAM * 4) && A((void **)&n.Wb, 3 * WID * WID * 2) &&
               A((void **)&n.Z, (size_t)4 * n.bmax * WID * 4) && A((void **)&n.D, (size_t)2 * n.bmax * WID * 4) &&
+              A((void **)&n.Gp, (size_t)(n.bmax / WID) * NPARAM * 4) && A((void **)&n.Lp, (size_t)(n.bmax / WID) * 4) &&
               A((void **)&n.Y, (size_t)n.bmax * 4) && A((void **)&n.DY, (size_t)n.bmax * 4) &&
               A((void **)&n.loss, 4) && A((void **)&n.err, 4);
     if (!ok) {
@@ -701,7 +705,7 @@ void mlp_destroy(sdpd_mlp *h)
     if (!h) return;
     cudaDeviceSynchronize();
     Net &n = h->net;
-    void *ps[] = { n.P, n.G, n.M, n.V, n.Wb, n.Z, n.D, n.Y, n.DY, n.loss, n.err };
+    void *ps[] = { n.P, n.G, n.M, n.V, n.Wb, n.Z, n.D, n.Gp, n.Lp, n.Y, n.DY, n.loss, n.err };
     for (void *p : ps) cudaFree(p);
     delete h;
 }
@@ -737,7 +741,9 @@ sdpd_status mlp_gradients(sdpd_mlp *h, const float *X, const float *T, int batch
     if (batch < 1 || batch > h->net.bmax) return mlp_fail(SDPD_E_INVALID, "mlp_gradients: batch out of range");
     cudaStream_t st = (cudaStream_t)stream;
     (void)cudaGetLastError();
-    k_mlp_grad<<<1, 128, SMEM_BYTES, st>>>(h->net, X, T, batch);
+    const int ntile = (batch + WID - 1) / WID;
+    k_mlp_grad<<<ntile, 128, SMEM_BYTES, st>>>(h->net, X, T, batch);
+    k_mlp_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(h->net, ntile, batch);
     if (cudaGetLastError() != cudaSuccess) return mlp_fail(SDPD_E_CUDA, "mlp_gradients: launch");
     if (loss) {
         if (cudaMemcpyAsync(loss, h->net.loss, 4, cudaMemcpyDefault, st) != cudaSuccess ||
