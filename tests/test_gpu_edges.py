@@ -42,8 +42,10 @@ def test_single_particle(precision):
     o.evaluate(1)
     so = o.state()
     assert sim.pairs().shape[0] == 0
-    assert g["d"][0] == pytest.approx(so["d"][0], rel=1e-12)
-    np.testing.assert_allclose(g["F"], so["F"], rtol=1e-12, atol=0)
+    # the self term W(0) alone; the split path sums in FP32
+    tol = 1e-12 if precision == B.SDPD_PREC_FP64 else 1e-6
+    assert g["d"][0] == pytest.approx(so["d"][0], rel=tol)
+    np.testing.assert_allclose(g["F"], so["F"], rtol=tol, atol=0)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
@@ -77,8 +79,10 @@ def test_pairs_straddling_h(precision):
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_empty_instance_in_a_batch(precision):
-    a = cases.poiseuille_si(nx=12, ny=12, nz=12, seed=2)
-    b = cases.sedimentation(nx=12, ny=12, nz=24)
+    # the random stream is keyed by the instance index: without it the
+    # instances of the batch repeat their single runs bit for bit
+    a = cases.poiseuille_si(nx=12, ny=12, nz=12, seed=2, coeff_t=0.0)
+    b = cases.sedimentation(nx=12, ny=12, nz=24, coeff_t=0.0)
     empty = _subset(cases.poiseuille_si(nx=12, ny=12, nz=12, seed=3), np.array([], dtype=np.int64))
     batch = B.Sim([a, empty, b], precision=precision)
     batch.step(3)
@@ -104,7 +108,10 @@ def test_dry_granular_matches_oracle():
     o.run(6)
     g, so = sim.state(density=False), o.state()
     assert rel_l2(g["v"], so["v"]) < 1e-9
-    assert rel_l2(g["w"], so["w"]) < 1e-9
+    # spins may stay at rounding level (no sliding contact yet): compare on
+    # the scale of v / R
+    scale = np.linalg.norm(so["v"]) / np.mean(c["radius"])
+    assert np.linalg.norm(g["w"] - so["w"]) <= 1e-9 * scale
 
 
 def test_network_on_empty_single_and_one_row():
