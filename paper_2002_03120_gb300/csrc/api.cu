@@ -772,7 +772,7 @@ sdpd_status sdpd_couple_drag(sdpd_ctx *c, void *stream)
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
     (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->density_valid) return fail(SDPD_E_STATE, "sdpd_compute_density must precede sdpd_couple_drag");
-    launch_drag(c->b, (cudaStream_t)stream);
+    launch_drag(c->b, c->precision, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     c->drag_valid = true;
     return SDPD_OK;
@@ -836,12 +836,12 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         cudaStream_t cs = c->cap_stream;
         enqueue_build(c, cs, c->b.need_build);
         launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, c->b.fresh, cs);
-        launch_drag(c->b, cs);
+        launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 1, c->newton3, cs);
         launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
         enqueue_build(c, cs, c->b.need_build);
         launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, nullptr, cs);
-        launch_drag(c->b, cs);
+        launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 2, c->newton3, cs);
         launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);
         launch_step_done(c->b, cs);

@@ -467,6 +467,7 @@ __device__ __forceinline__ void block_sum_to_t0(double (&v)[K], double (*red)[K]
 // (s included), v_f = sum W v / sum W over fluid neighbours, drag along
 // (v_f - v_s) with the Ergun (eps <= 0.8) or Wen-Yu (eps > 0.8) coefficient in
 // the closed form that stays finite at eps -> 1 and |v_f - v_s| -> 0.
+template <class R>
 __global__ void __launch_bounds__(RB) k_drag(Bufs b)
 {
     __shared__ double red[RB / 32][5];
@@ -479,6 +480,39 @@ __global__ void __launch_bounds__(RB) k_drag(Bufs b)
     const double Ri = b.R[g];
     double Vsum = 0.0, S = 0.0, U0 = 0.0, U1 = 0.0, U2 = 0.0;
     const int n = b.ncnt[s];
+    if constexpr (sizeof(R) == 4) {
+        // split precision: the kernel-weighted fluid sums in FP32 on the
+        // mirrors (exact r < h decision of Rel); the volumes in FP64
+        const Geo<float> geo(I);
+        const float4 *__restrict__ A = b.A32;
+        const float4 *__restrict__ Bm = Mir<float>::B(b);
+        const float4 Ai = A[s];
+        const float Wc = K<float>::Wc(I), irc = K<float>::inv_rc(I);
+        float Sf = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
+        for (int k = threadIdx.x; k < n; k += RB) {
+            const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
+            if (e & NB_FAR) continue;
+            const int j = (int)e;
+            const float4 Aj = A[j];
+            const int tj = mir_type(Aj);
+            if (tj != T_RIGID && tj != T_FLUID) continue;
+            float rx, ry, rz, r2;
+            if (!Rel<float>::get(b, I, geo, Ai, Aj, g, j, rx, ry, rz, r2)) continue;
+            if (tj == T_RIGID) {
+                const double Rj = b.R[b.perm[j]];
+                Vsum += 4.0 / 3.0 * PI * Rj * Rj * Rj;
+            } else {
+                const float q = sqrtf(r2) * irc, om = 1.f - q;
+                const float W = Wc * (1.f + 3.f * q) * om * om * om;
+                const float4 Bj = Bm[j];
+                Sf += W;
+                u0 += W * Bj.x;
+                u1 += W * Bj.y;
+                u2 += W * Bj.z;
+            }
+        }
+        S = Sf; U0 = u0; U1 = u1; U2 = u2;
+    } else
     for (int k = threadIdx.x; k < n; k += RB) {
         const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
         if (e & NB_FAR) continue;
@@ -1057,6 +1091,7 @@ __device__ __forceinline__ void hist_put(const Bufs &b, int r, int slot, int par
 // wall planes, drag, gravity.  Lanes stride over the neighbour list in rounds
 // of 32; new history entries go to round-major, lane-minor slots (ballot),
 // so the table is deterministic.
+template <class R>
 __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
 {
     __shared__ double red[RB / 32][15];
@@ -1078,6 +1113,42 @@ __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
     int base = 0;
     const int n = b.ncnt[s];
     // fluid neighbours: F^C + F^D of each pair (s, j), summed for Eq. F_fpi_PG
+    if constexpr (sizeof(R) == 4) {
+        // split precision: the pair arithmetic in FP32 on the mirrors, as
+        // for fluid pairs (the C + D part of the SDPD pair; the exact r < h
+        // decision of Rel); DEM and lubrication below stay FP64
+        const PairK<float> P(I, 0u);
+        const Geo<float> geo(I);
+        const float4 *__restrict__ A = b.A32;
+        const float4 *__restrict__ Bm = Mir<float>::B(b);
+        const float4 *__restrict__ Cm = Mir<float>::C(b);
+        const float4 *__restrict__ Dm = Mir<float>::D(b);
+        const float4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
+        const float Rf = (float)Ri;
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
+        for (int k = threadIdx.x; k < n; k += RB) {
+            const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
+            if (e & NB_FAR) continue;
+            const int j = (int)e;
+            const float4 Aj = A[j];
+            if (mir_type(Aj) != T_FLUID) continue;
+            float rx, ry, rz, r2;
+            if (!Rel<float>::get(b, I, geo, Ai, Aj, g, j, rx, ry, rz, r2)) continue;
+            Z6<float> z;
+            float ox, oy, oz, ce, ex, ey, ez, q, om;
+            sdpd_pair<float>(P, rx, ry, rz, r2, Bi, Ci, Di, Bm[j], Cm[j], Dm[j], false, 0, z, ox, oy, oz, ce,
+                             ex, ey, ez, q, om);
+            f0 += ox + ce * ex;
+            f1 += oy + ce * ey;
+            f2 += oz + ce * ez;
+            // lever -R e: (-R e) x (o + ce e) = -R e x o
+            t0 -= Rf * (ey * oz - ez * oy);
+            t1 -= Rf * (ez * ox - ex * oz);
+            t2 -= Rf * (ex * oy - ey * ox);
+        }
+        acc[0] = f0; acc[1] = f1; acc[2] = f2;
+        acc[3] = t0; acc[4] = t1; acc[5] = t2;
+    } else
     for (int k = threadIdx.x; k < n; k += RB) {
         const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
         if (e & NB_FAR) continue;
@@ -1245,9 +1316,11 @@ void launch_density(const Bufs &b, int precision, int dflags, int newton3, const
     }
 }
 
-void launch_drag(const Bufs &b, cudaStream_t st)
+void launch_drag(const Bufs &b, int precision, cudaStream_t st)
 {
-    if (b.nrigid) k_drag<<<b.nrigid, RB, 0, st>>>(b);
+    if (!b.nrigid) return;
+    if (precision == SDPD_PREC_SPLIT) k_drag<float><<<b.nrigid, RB, 0, st>>>(b);
+    else k_drag<double><<<b.nrigid, RB, 0, st>>>(b);
 }
 
 
@@ -1270,7 +1343,8 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
         k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b);
     }
     if (b.nrigid) {
-        k_force_rigid<<<b.nrigid, RB, 0, st>>>(b, velver);
+        if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<b.nrigid, RB, 0, st>>>(b, velver);
+        else k_force_rigid<double><<<b.nrigid, RB, 0, st>>>(b, velver);
         if (velver == 2) k_hist_copy<<<nblk(b.nrigid, 64), 64, 0, st>>>(b);
     }
 }

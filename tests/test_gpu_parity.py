@@ -83,18 +83,21 @@ def test_forces_velver2_with_history(precision):
     assert rel_l2(sim.state()["F"], orc.state()["F"]) < TOL_FORCE[precision]
 
 
+@pytest.mark.parametrize("precision,tol_f", [(B.SDPD_PREC_FP64, 1e-11), (B.SDPD_PREC_SPLIT, 1e-5)])
 @pytest.mark.parametrize("name", ["sediment_small", "slurry_small", "dambreak_small"])
-def test_drag_parity(name):
+def test_drag_parity(name, precision, tol_f):
+    # eps from the rigid volumes (FP64, exact decisions) in both precisions;
+    # the kernel-weighted fluid velocity in FP32 on the split path
     case = dict(CASES[name])
     rng = np.random.default_rng(4)
     case["v"] = np.where((case["type"] <= 1)[:, None], rng.normal(0, 0.05, case["v"].shape), 0.0)
-    sim = _gpu_eval(case, B.SDPD_PREC_FP64)
+    sim = _gpu_eval(case, precision)
     orc = _oracle_eval(case)
     eps_g, F_g = sim.drag()
     eps_o, _ = orc.fpi()
     rig = np.where(case["type"] == 1)[0]
     assert np.allclose(eps_g, eps_o[rig], rtol=1e-13, atol=0)
-    assert rel_l2(F_g, orc.component("dg")[rig]) < 1e-11
+    assert rel_l2(F_g, orc.component("dg")[rig]) < tol_f
 
 
 def test_config2_full_size_parity():
