@@ -218,18 +218,6 @@ __device__ __forceinline__ bool pair_owned(long long s, int j, int base)
     return low_owns == (s < j);
 }
 
-struct NbWriter {
-    const Bufs &b;
-    long long s, Np;
-    int cnt;
-    bool rig;
-    __device__ __forceinline__ void put(uint32_t entry, int tj)
-    {
-        if (cnt < b.cap) b.nbr[(long long)cnt * Np + s] = (int)entry;
-        ++cnt;
-        rig |= (tj == T_RIGID);
-    }
-};
 
 __device__ __forceinline__ bool nb_test(const Bufs &b, const Inst &I, const float4 &Ai, int ti, float Ri,
                                         int j, float sx, float sy, float sz, uint32_t &entry, int &tj)
@@ -260,35 +248,55 @@ __global__ void k_neighbors(Bufs b, const int *gate)
     const float4 Ai = b.A32[s];
     const int *adj = b.cell_adj + (long long)b.skey[s] * 27;
     const int base = b.cstart[I.cell_base];  // first slot of the instance
-    NbWriter W{ b, s, b.Npad, 0, false };
+    const long long Np = b.Npad;
+    int *col = b.nbr + s;                     // this particle's column, entry k at col[k * Np]
+    const int cap = b.cap;
+    // one scan in ascending slot order: owned pairs from the front, the
+    // others from the back of the column (so in descending positions)
+    int nf = 0, m = 0;
+    bool rig = false;
     uint32_t entry;
     int tj;
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool want_owned = (pass == 0);
-        for (int q = 0; q < 27; ++q) {
-            const int code = adj[q];
-            if (code < 0) break;
-            const int key = code >> 5, oc = code & 31;
-            const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
-                        sz = (float)(oc / 9 - 1) * I.csf[2];
-            const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
-            for (int j = j0; j < j1; ++j) {
-                if (j == s || pair_owned(s, j, base) != want_owned) continue;
-                if (nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) W.put(entry, tj);
+    for (int q = 0; q < 27; ++q) {
+        const int code = adj[q];
+        if (code < 0) break;
+        const int key = code >> 5, oc = code & 31;
+        const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
+                    sz = (float)(oc / 9 - 1) * I.csf[2];
+        const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
+        for (int j = j0; j < j1; ++j) {
+            if (j == s || !nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) continue;
+            rig |= (tj == T_RIGID);
+            if (pair_owned(s, j, base)) {
+                if (nf + m < cap) col[(long long)nf * Np] = (int)entry;
+                ++nf;
+            } else {
+                if (nf + m < cap) col[(long long)(cap - 1 - m) * Np] = (int)entry;
+                ++m;
             }
         }
-        if (pass == 0) {
-            if (W.cnt > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
-            b.nfirst[s] = min(W.cnt, min(b.cap, b.capown));
-        }
     }
-    int cnt = W.cnt;
-    if (cnt > b.cap) {
+    const int n = nf + m;
+    if (nf > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+    if (n > cap) {
         atomicOr(b.err, ERR_NBR_CAP);
-        cnt = b.cap;
+    } else {
+        // the back region [cap - m, cap) holds the non-owned entries in
+        // descending order: reverse it in place, then move it down to
+        // [nf, n) in ascending order (destination below the source, so an
+        // ascending copy never overwrites an entry still to be read)
+        for (int k = 0; k < m / 2; ++k) {
+            const long long a = (long long)(cap - m + k) * Np, c = (long long)(cap - 1 - k) * Np;
+            const int t = col[a];
+            col[a] = col[c];
+            col[c] = t;
+        }
+        if (nf < cap - m)
+            for (int k = 0; k < m; ++k) col[(long long)(nf + k) * Np] = col[(long long)(cap - m + k) * Np];
     }
-    b.ncnt[s] = cnt;
-    b.nbflag[s] = W.rig ? 1 : 0;
+    b.nfirst[s] = min(nf, min(cap, b.capown));
+    b.ncnt[s] = min(n, cap);
+    b.nbflag[s] = rig ? 1 : 0;
 }
 
 // For every non-owned entry of s (positions [nfirst, n)), the position of s
