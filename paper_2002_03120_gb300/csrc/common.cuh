@@ -204,12 +204,11 @@ __device__ __forceinline__ void bm_sincos_w(uint32_t w, double &s, double &c)
     const double2 sc = __ldg(&BM_SC_TAB[h]);
     const double sa = fma(sc.x, cl, sc.y * sl);
     const double ca = fma(sc.y, cl, -(sc.x * sl));
-    s = (q & 1) ? ca : sa;
-    c = (q & 1) ? -sa : ca;
-    if (q & 2) {
-        s = -s;
-        c = -c;
-    }
+    // quadrant: swap and sign flips on the bit patterns (integer pipe)
+    const unsigned long long SIGN = 0x8000000000000000ull;
+    const unsigned long long fs = (q & 2) ? SIGN : 0ull, fc = ((q + 1) & 2) ? SIGN : 0ull;
+    s = __longlong_as_double((long long)((unsigned long long)__double_as_longlong((q & 1) ? ca : sa) ^ fs));
+    c = __longlong_as_double((long long)((unsigned long long)__double_as_longlong((q & 1) ? sa : ca) ^ fc));
 }
 
 template <class R> struct BoxMuller;
@@ -271,24 +270,35 @@ template <> struct Geo<float> {
         rz = (Ai.z - Aj.z) + (float)d2 * c2;
     }
 };
+// |x| compared through the IEEE bit patterns, which order like the values
+// for non-negative numbers: an exact test that runs on the integer pipe and
+// leaves the FP64 pipe (the bound of the FP64 pair kernels) to arithmetic.
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 template <> struct Geo<double> {
     bool p0, p1, p2;
     double L0, L1, L2;
+    unsigned long long h0, h1, h2;   // bits of L/2
     __device__ __forceinline__ explicit Geo(const Inst &I)
         : p0(I.periodic[0]), p1(I.periodic[1]), p2(I.periodic[2]), L0(I.box[0]), L1(I.box[1]),
-          L2(I.box[2]) {}
-    __device__ __forceinline__ static double img(double d, bool p, double L)
+          L2(I.box[2]), h0(abs_bits(0.5 * I.box[0])), h1(abs_bits(0.5 * I.box[1])),
+          h2(abs_bits(0.5 * I.box[2])) {}
+    // minimum image: d - L if d > L/2, d + L if d < -L/2 (the same operations
+    // as the oracle; the rare wrap is a branch)
+    __device__ __forceinline__ static double img(double d, bool p, double L, unsigned long long hb)
     {
-        if (!p) return d;
-        const double h = 0.5 * L;
-        return d > h ? d - L : (d < -h ? d + L : d);
+        if (p && abs_bits(d) > hb) d = d > 0.0 ? d - L : d + L;
+        return d;
     }
     __device__ __forceinline__ void disp(const double4_32a &Ai, const double4_32a &Aj, double &rx,
                                          double &ry, double &rz) const
     {
-        rx = img(Ai.x - Aj.x, p0, L0);
-        ry = img(Ai.y - Aj.y, p1, L1);
-        rz = img(Ai.z - Aj.z, p2, L2);
+        rx = img(Ai.x - Aj.x, p0, L0, h0);
+        ry = img(Ai.y - Aj.y, p1, L1, h1);
+        rz = img(Ai.z - Aj.z, p2, L2, h2);
     }
 };
 

@@ -31,6 +31,11 @@ template <class R> struct Vec2;
 template <> struct Vec2<float> { using T2 = float2; };
 template <> struct Vec2<double> { using T2 = double2; };
 
+// a < b for a, b >= 0: the value compare in FP32, the bit-pattern compare
+// (same result, integer pipe) in FP64
+__device__ __forceinline__ bool lt_nonneg(float a, float b) { return a < b; }
+__device__ __forceinline__ bool lt_nonneg(double a, double b) { return abs_bits(a) < abs_bits(b); }
+
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
@@ -110,7 +115,7 @@ template <> struct Rel<double> {
     {
         geo.disp(Ai, Aj, rx, ry, rz);
         r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
-        return r2 < I.rc2;
+        return abs_bits(r2) < abs_bits(I.rc2);   // r2 >= 0: the bit order is the value order
     }
 };
 
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
             }
             // float: correctly rounded sqrt; double: r2 / sqrt via rsqrt (~1 ulp)
             const R q = (sizeof(R) == 4 ? sqrt(r2) : r2 * rsqrt_<R>(r2)) * irc;
-            const R om = q < R(1) ? R(1) - q : R(0);
+            const R om = lt_nonneg(q, R(1)) ? R(1) - q : R(0);
             acc.add(Wc * (R(1) + R(3) * q) * om * om * om);
         }
         d = I.Cn * acc.value();
@@ -249,7 +254,7 @@ __device__ __forceinline__ void density_half_slot(const Bufs &b, long long s)
             double rx, ry, rz, r2;
             if (Rel<double>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) {
                 const double q = r2 * rsqrt_<double>(r2) * K<double>::inv_rc(I);
-                const double om = q < 1.0 ? 1.0 - q : 0.0;
+                const double om = lt_nonneg(q, 1.0) ? 1.0 - q : 0.0;
                 W = K<double>::Wc(I) * (1.0 + 3.0 * q) * om * om * om;
                 acc = __dadd_rn(acc, W);
                 if (want_close && r2 <= close_r2) {
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(256) k_reinit(Bufs b, int any_filter, const in
             R rx, ry, rz, r2;
             if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
             const R q = sqrt(r2) * irc;
-            const R om = q < R(1) ? R(1) - q : R(0);
+            const R om = lt_nonneg(q, R(1)) ? R(1) - q : R(0);
             const R W = Wc * (R(1) + R(3) * q) * om * om * om;
             num.add(W);
             den.add(W / (R)b.sd[e]);
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(256) k_filter(Bufs b, const int *gate)
             R rx, ry, rz, r2;
             if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
             const R q = sqrt(r2) * irc;
-            const R om = q < R(1) ? R(1) - q : R(0);
+            const R om = lt_nonneg(q, R(1)) ? R(1) - q : R(0);
             const R W = Wc * (R(1) + R(3) * q) * om * om * om;
             num.add((R)b.sp[e] * W);
             den.add(W);
@@ -647,7 +652,7 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R
     const R is2 = R(0.70710678118654752440);
     const R ir = rsqrt_<R>(r2);
     q = r2 * ir * P.irc;
-    om = q < R(1) ? R(1) - q : R(0);
+    om = lt_nonneg(q, R(1)) ? R(1) - q : R(0);
     const R Fk = P.Fc * om * om;
     ex = rx * ir; ey = ry * ir; ez = rz * ir;
     const R vx = Bi.x - Bj.x, vy = Bi.y - Bj.y, vz = Bi.z - Bj.z;

@@ -13,7 +13,7 @@ not have:
   3. inference on 10^6 query points on the tensor cores;
   4. proposal of sweep points (a target viscosity, or the largest ensemble
      disagreement), every proposal re-checked by the simulation, which stays
-     both the fallback and the judge of the surrogate's error.
+     both the fallback and the arbiter of the surrogate's error.
 
 Instances are in the paper's mesoscale units (rho0 = 3, p0 = beta = 100,
 alpha = 7, r_c = 3.9 dx); the viscosity follows an Arrhenius law in T scaled to
