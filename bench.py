@@ -106,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -494,6 +494,8 @@ def main():
                    "parallelism": f"replicas x{ws}",
                    "tuning": main_r["setting"] or "defaults (newton3 1, skin 0.03, block 128)"},
         "timesteps_per_s": steps_per_s,
+        "step_ms": {"min": float(np.min(main_r["per_step"])), "median": float(np.median(main_r["per_step"])),
+                    "max": float(np.max(main_r["per_step"]))},
         "gpu_launches": main_r["kernels"] * args.steps,
         "clocks": main_r["clocks"],
         "roofline": {"kernel": ("force pass (k_force_half + k_force_gather + k_force_rigid), velver 1"
