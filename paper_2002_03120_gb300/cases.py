@@ -190,6 +190,47 @@ def poiseuille_meso_walls(nx=12, ny=24, nz=12, layers=4, **kw) -> dict:
     return case
 
 
+def buoyancy_column(nx=12, ny=12, nz=24, layers=4, g=0.5, rho_ratio=1.0, diam_dx=4.0, eta=25.0,
+                    kBT=1e-4, seed=1, **over) -> dict:
+    """A fluid column in the paper's mesoscale units (rho0 = 3, p0 = beta = 100,
+    alpha = 7, unit mass), periodic in x and y, with dummy-particle walls below
+    and above in z, gravity -g along z, and one sphere of diameter diam_dx dx
+    and density rho_ratio rho0 at mid-height replacing the nearest lattice
+    site (the buoyancy check of the pressure-gradient force, Eq. F_fpi_PG)."""
+    rho0 = 3.0
+    dx = rho0 ** (-1.0 / 3.0)
+    params = base_params(dx=dx, rho0=rho0, eta=eta, alpha=7.0, **over)
+    params.update(p0=100.0, beta_p=100.0, kBT=kBT, r_c=3.9 * dx, box=[nx * dx, ny * dx, nz * dx],
+                  periodic=[1, 1, 0], g=[0.0, 0.0, -g], seed=seed, dem_law=1, kn=1e3, restitution=0.9)
+    c = math.sqrt(params["alpha"] * params["p0"] / rho0)
+    params["dt"] = min(0.1 * params["r_c"] / c, 0.3 / eta)
+    for k, v in over.items():
+        params[k] = v
+    rng = np.random.default_rng(seed)
+    sites = lattice(nx, ny, nz, dx)
+    target = np.array([0.5 * nx * dx, 0.5 * ny * dx, 0.5 * nz * dx])
+    s = int(np.argmin(np.sum((sites - target) ** 2, axis=1)))
+    centre = sites[s].copy()
+    fluid = _jitter(np.delete(sites, s, axis=0), 0.01 * dx, rng)
+    wx, wt = _wall_layers((nx, ny, nz), dx, (0, 0, 0), layers, [(2, 0), (2, 1)])
+    R = 0.5 * diam_dx * dx
+    ms = rho_ratio * rho0 * 4.0 / 3.0 * math.pi * R ** 3
+    nf = len(fluid)
+    parts = [
+        (fluid, T_FLUID, np.full(nf, 0.5 * dx), np.full(nf, 1.0)),
+        (centre[None, :], T_RIGID, np.array([R]), np.array([ms])),
+    ]
+    case = _assemble(params, parts, f"buoyancy_column_{nx}x{ny}x{nz}")
+    nw = len(wx)
+    case["x"] = np.concatenate([case["x"], wx])
+    case["type"] = np.concatenate([case["type"], wt])
+    case["radius"] = np.concatenate([case["radius"], np.full(nw, 0.5 * dx)])
+    case["mass"] = np.concatenate([case["mass"], np.full(nw, 1.0)])
+    case["v"] = np.zeros_like(case["x"])
+    case["w"] = np.zeros_like(case["x"])
+    return case
+
+
 def _place_spheres_on_sites(nxyz, n_target: int, diam_dx: np.ndarray, periodic,
                             rng: np.random.Generator):
     """Random sequential addition on the sites of an nx x ny x nz lattice
