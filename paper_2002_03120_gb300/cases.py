@@ -190,7 +190,7 @@ def poiseuille_meso_walls(nx=12, ny=24, nz=12, layers=4, **kw) -> dict:
     return case
 
 
-def buoyancy_column(nx=12, ny=12, nz=24, layers=4, g=0.5, rho_ratio=1.0, diam_dx=4.0, eta=25.0,
+def buoyancy_column(nx=14, ny=14, nz=24, layers=4, g=0.5, rho_ratio=1.0, diam_dx=4.0, eta=25.0,
                     kBT=1e-4, seed=1, **over) -> dict:
     """A fluid column in the paper's mesoscale units (rho0 = 3, p0 = beta = 100,
     alpha = 7, unit mass), periodic in x and y, with dummy-particle walls below
