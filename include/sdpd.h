@@ -208,11 +208,20 @@ sdpd_status sdpd_count_pairs(sdpd_ctx *ctx, long long *n_pairs);
 sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
 
 /* Force-pass variant: newton3 = 1 (default) evaluates each unordered pair once
- * (the lower slot owns it, its result goes to the partner through a pair
- * buffer; deterministic, no atomics); newton3 = 0 evaluates every pair from
- * both sides.  Both give the same forces up to summation order.  Invalidates
- * the current neighbour build and graph.  Synchronous. */
+ * (one of the two particles owns it, chosen by a hash of the pair so that
+ * each owns about half of its list; its result goes to the partner through a
+ * pair buffer; deterministic, no atomics); newton3 = 0 evaluates every pair
+ * from both sides.  Both give the same forces up to summation order.
+ * Invalidates the current neighbour build and graph.  Synchronous. */
 sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
+
+/* Normals cache (default on = 1): the second force evaluation of a step
+ * (velver 2) reads the six standard normals of each pair that the first one
+ * drew, where the neighbour list was not rebuilt in between, instead of
+ * drawing them again.  The draws are keyed by (pair, step) (Section 2.1,
+ * Eq. FijT; one dW per pair and step), so both give the same bits; off
+ * (0) draws every time.  Invalidates the current graph.  Synchronous. */
+sdpd_status sdpd_set_noise_cache(sdpd_ctx *ctx, int on);
 
 /* Threads per block of the pair kernels (density, filter, force passes):
  * 64, 128 (default) or 256.  A tuning knob; results do not change.

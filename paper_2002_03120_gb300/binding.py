@@ -72,7 +72,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_compute_density", "sdpd_couple_drag", "sdpd_compute_forces", "sdpd_integrate",
            "sdpd_step", "sdpd_viscosity_probe", "sdpd_get_state", "sdpd_get_drag",
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
-           "sdpd_set_force_mode", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
+           "sdpd_set_force_mode", "sdpd_set_noise_cache", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
            "sdpd_check",
            "sdpd_last_error", "sdpd_noise_normals", "sdpd_viscosity_fit", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
            "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
         "sdpd_diagnostics": (st, [vp, C.c_int, dp]),
         "sdpd_graph_kernels": (st, [vp, llp]),
         "sdpd_set_force_mode": (st, [vp, C.c_int]),
+        "sdpd_set_noise_cache": (st, [vp, C.c_int]),
         "sdpd_set_skin": (st, [vp, C.c_double]),
         "sdpd_set_block_size": (st, [vp, C.c_int]),
         "sdpd_density_noalloc": (st, [C.POINTER(SdpdParams), C.c_longlong, vp, vp, vp, vp, vp]),
@@ -342,6 +343,9 @@ class Sim:
 
     def set_force_mode(self, newton3: int):
         _check(load().sdpd_set_force_mode(self._h, int(newton3)))
+
+    def set_noise_cache(self, on: bool):
+        _check(load().sdpd_set_noise_cache(self._h, int(bool(on))))
 
     def set_block_size(self, threads: int):
         _check(load().sdpd_set_block_size(self._h, int(threads)))

@@ -54,6 +54,7 @@ struct sdpd_ctx {
     int any_filter = 0, any_artvis = 0, any_reinit = 0;
     std::vector<double> probe_y;   // mean slab positions of the last viscosity probe
     int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct
+    int noise_cache = 1;               // second evaluation of a step reuses the first one's normals
     double skin = 0.03;                // Verlet skin as a fraction of h
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
     int sticky_err = 0;
@@ -381,7 +382,7 @@ sdpd_status ensure_geometry(sdpd_ctx *c)
 
 void enqueue_build(sdpd_ctx *c, cudaStream_t st, const int *gate = nullptr)
 {
-    c->b.use_cache = c->newton3;
+    c->b.use_cache = c->noise_cache;
     launch_build(c->b, c->precision, c->newton3, gate, st);
 }
 
@@ -464,34 +465,41 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     IALLOC(b.nbflag, N);
     IALLOC(b.rev, (size_t)c->cap * c->Npad);
     // each particle owns about half of its list (hash ownership, spread of a
-    // few pairs): the pair buffer and the normals cache hold cap/2 + 64 rows
+    // few pairs): the pair buffer and the normals cache of the Newton-3 pass
+    // hold cap/2 + 64 rows.  The direct pass instead caches the normals of
+    // every list entry ([cap][Npad]).  A context runs one force pass at a
+    // time, so both layouts share one arena.
     b.capown = std::min(c->cap, c->cap / 2 + 64);
     {
         const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
-        char *pa = nullptr, *pb = nullptr, *oa = nullptr, *ob = nullptr;
-        IALLOC(pa, 4 * rs * (size_t)b.capown * c->Npad);
+        const size_t Np = (size_t)c->Npad, own = (size_t)b.capown * Np, all = (size_t)c->cap * Np;
         // the split path keeps {o, ce} in resA only
-        IALLOC(pb, precision == SDPD_PREC_SPLIT ? 16 : 2 * rs * (size_t)b.capown * c->Npad);
+        const size_t n_resA = 4 * rs * own, n_resB = precision == SDPD_PREC_SPLIT ? 0 : 2 * rs * own;
+        const size_t n_zA = 4 * rs * own, n_zB = 2 * rs * own;
+        const size_t half_bytes = n_resA + n_resB + n_zA + n_zB, direct_bytes = 6 * rs * all;
+        char *arena = nullptr, *oa = nullptr, *ob = nullptr, *dummy = nullptr;
+        IALLOC(arena, std::max(half_bytes, direct_bytes));
+        IALLOC(dummy, 16);
         IALLOC(oa, 4 * rs * (size_t)N);
         IALLOC(ob, 2 * rs * (size_t)N);
-        b.resA = pa; b.resB = pb; b.ownA = oa; b.ownB = ob;
+        b.resA = arena;
+        b.resB = n_resB ? arena + n_resA : dummy;
+        b.zA = arena + n_resA + n_resB;
+        b.zB = arena + n_resA + n_resB + n_zA;
+        b.zdA = arena;
+        b.zdB = arena + 4 * rs * all;
+        b.ownA = oa; b.ownB = ob;
     }
     IALLOC(b.xl64, N); IALLOC(b.dsp, N);
     IALLOC(b.aclose, N); IALLOC(b.aclose_ok, 1); IALLOC(b.sdr, N); IALLOC(b.xs, 3 * N);
     IALLOC(b.need_build, 1); IALLOC(b.fresh, 1);
     IALLOC(b.list_epoch, 1); IALLOC(b.cache_epoch, 1); IALLOC(b.cache_step, 1);
-    {
-        const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
-        char *za = nullptr, *zb = nullptr;
-        IALLOC(za, 4 * rs * (size_t)b.capown * c->Npad);
-        IALLOC(zb, 2 * rs * (size_t)b.capown * c->Npad);
-        b.zA = za; b.zB = zb;
-    }
     b.use_cache = 1;
     IALLOC(b.step, 1); IALLOC(b.err, 1); IALLOC(b.pair_count, 1); IALLOC(b.work, 1);
     IALLOC(b.probe, 4096 * 3 + 64);
 #undef IALLOC
-    if (cudaMemset(b.need_build, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.fresh, 0, sizeof(int)) != cudaSuccess ||
+    if (cudaMemset(b.rev, 0, sizeof(uint16_t) * (size_t)c->cap * c->Npad) != cudaSuccess ||
+        cudaMemset(b.need_build, 0, sizeof(int)) != cudaSuccess || cudaMemset(b.fresh, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b.aclose_ok, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b.list_epoch, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(b.cache_epoch, 0xFF, sizeof(unsigned)) != cudaSuccess ||
@@ -865,6 +873,19 @@ sdpd_status sdpd_set_force_mode(sdpd_ctx *c, int newton3)
     CUDA_TRY(cudaDeviceSynchronize());
     if (newton3 != c->newton3) {
         c->newton3 = newton3;
+        drop_graph(c);
+        c->cells_valid = c->density_valid = c->drag_valid = false;
+    }
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_set_noise_cache(sdpd_ctx *c, int on)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (on != 0 && on != 1) return fail(SDPD_E_INVALID, "on must be 0 or 1");
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (on != c->noise_cache) {
+        c->noise_cache = on;
         drop_graph(c);
         c->cells_valid = c->density_valid = c->drag_valid = false;
     }

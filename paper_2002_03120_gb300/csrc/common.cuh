@@ -86,14 +86,18 @@ struct Bufs {
     // neighbour lists: owned pairs first (Newton-3 ownership), see k_neighbors
     int *nbr, *ncnt, *nfirst;  // nfirst = length of the owned prefix
     int *skey;                 // cell key per slot
-    uint16_t *rev;             // non-owned entry k of s -> position of s in the partner's list
+    uint16_t *rev;             // owned entry k of s -> row of the partner's column that
+                               // receives s's result of the pair (its non-owned entry - nfirst);
+                               // non-owned entry k of s -> position of s in the partner's list
     uint8_t *nbflag;           // per slot: bit 0 = has a rigid neighbour
     int capown;                // owned entries per particle in the pair buffer
     double *rm, *rI;           // [N] 1/m and 1/I rounded to nearest (the update divides with them)
     uint8_t *aclose;           // [N] slot has a mobile neighbour within the collision radius
     int *aclose_ok;            // the marks belong to the current positions and list
     void *resA, *resB;         // pair results [capown][Npad]: FP64 R4 {f, h.x}, R2 {h.y, h.z}
-                               // (h = e x o); split float4 {o, ce}, resB unused
+                               // (h = e x o) in the column of the particle that does not own
+                               // the pair, row = its non-owned entry - nfirst; split float4
+                               // {o, ce} in the owner's column at the owned entry, resB unused
     void *ownA, *ownB;         // per slot sums of the owned pairs
     // fluid-particle interaction per rigid index
     double *eps, *fdg;         // eps [nr], drag [nr][3]
@@ -111,6 +115,7 @@ struct Bufs {
     unsigned *cache_epoch;     // list epoch of the cached normals
     long long *cache_step;     // step of the cached normals
     void *zA, *zB;             // normals [capown][Npad]: R4 {z0..z3}, R2 {z4, z5}
+    void *zdA, *zdB;           // direct pass: normals of every entry [cap][Npad] (same arena)
     int use_cache;
     int *fresh;                // a build happened since the last density
     // counters
@@ -218,8 +223,10 @@ template <> struct BoxMuller<double> {
         const double rad = sqrt(-2.0 * bm_log_w(((ua >> 9) << 1) | 1u));
         double s, c;
         bm_sincos_w(((ub >> 9) << 1) | 1u, s, c);
-        z0 = rad * c;
-        z1 = rad * s;
+        // rounded products: no later sum fuses them, so a normal read back
+        // from the cache and one drawn here enter the force identically
+        z0 = __dmul_rn(rad, c);
+        z1 = __dmul_rn(rad, s);
     }
 };
 template <> struct BoxMuller<float> {
@@ -230,8 +237,8 @@ template <> struct BoxMuller<float> {
         const float rad = sqrtf(-2.0f * logf(U1));
         float s, c;
         sincospif(2.0f * U2, &s, &c);
-        z0 = rad * c;
-        z1 = rad * s;
+        z0 = __fmul_rn(rad, c);
+        z1 = __fmul_rn(rad, s);
     }
 };
 

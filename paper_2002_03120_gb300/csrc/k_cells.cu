@@ -277,7 +277,8 @@ __global__ void k_neighbors(Bufs b, const int *gate)
         }
     }
     const int n = nf + m;
-    if (nf > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+    // the pair buffer holds capown rows of owned and of non-owned entries
+    if (nf > b.capown || m > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
     if (n > cap) {
         atomicOr(b.err, ERR_NBR_CAP);
     } else {
@@ -299,9 +300,12 @@ __global__ void k_neighbors(Bufs b, const int *gate)
     b.nbflag[s] = rig ? 1 : 0;
 }
 
-// For every non-owned entry of s (positions [nfirst, n)), the position of s
-// in the partner's owned prefix (ascending), by binary search; four searches
-// run interleaved so their loads overlap.
+// For every non-owned entry k of s (positions [nfirst, n)), the position r
+// of s in the partner j's owned prefix (ascending), by binary search; four
+// searches run interleaved so their loads overlap.  Both directions are kept,
+// in disjoint rows of rev: rev[k][s] = r (where s reads j's result in j's
+// column) and rev[r][j] = k - nfirst(s) (where j writes its result in s's
+// column); each owned entry of j gets exactly one.
 __device__ __forceinline__ int nb_at(const Bufs &b, int i, int k)
 {
     return (int)((uint32_t)__ldg(b.nbr + (long long)k * b.Npad + i) & ~NB_FAR);
@@ -345,8 +349,9 @@ __global__ void k_rev(Bufs b, const int *gate)
             const int k = k0 + g;
             if (k >= n) break;
             const bool ok = lo[g] < end[g] && nb_at(b, part[g], lo[g]) == (int)s;
-            if (!ok) atomicOr(b.err, ERR_REV);
+            if (!ok || k - first >= b.capown) atomicOr(b.err, ERR_REV);
             b.rev[(long long)k * Np + s] = (uint16_t)(ok ? lo[g] : 0);
+            if (ok && k - first < b.capown) b.rev[(long long)lo[g] * Np + part[g]] = (uint16_t)(k - first);
         }
     }
 }

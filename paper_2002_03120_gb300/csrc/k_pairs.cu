@@ -170,6 +170,35 @@ __device__ __forceinline__ long long next_warp_slots(const Bufs &b)
 
 // ------------------------------------------------------------------ density
 // gate: nullptr = always; else only when *gate != 0 (a build just happened)
+// Visits the entries k = 0 .. n-1 of a slot's neighbour list in order,
+// calling f(k, entry, record of the partner, side value of the partner).  The
+// list index two entries ahead and the record (and side value, when `side`
+// is given) one entry ahead are fetched before f runs on the current one, so
+// the loads of the next pair overlap this pair's arithmetic.  NB_FAR entries
+// are visited too (their record is fetched without the flag bit).
+template <class T4, class F>
+__device__ __forceinline__ void for_each_entry(const int *__restrict__ nb, long long Np, int n,
+                                               const T4 *__restrict__ A, const double *__restrict__ side, F &&f)
+{
+    if (n <= 0) return;
+    uint32_t en = (uint32_t)__ldg(nb);
+    uint32_t enn = n > 1 ? (uint32_t)__ldg(nb + Np) : 0u;
+    T4 An = A[en & ~NB_FAR];
+    double Sn = side ? side[en & ~NB_FAR] : 0.0;
+    for (int k = 0; k < n; ++k) {
+        const uint32_t e = en;
+        const T4 Aj = An;
+        const double Sj = Sn;
+        if (k + 1 < n) {
+            en = enn;
+            An = A[en & ~NB_FAR];
+            if (side) Sn = side[en & ~NB_FAR];
+            if (k + 2 < n) enn = (uint32_t)__ldg(nb + (long long)(k + 2) * Np);
+        }
+        f(k, e, Aj, Sj);
+    }
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const int *gate)
 {
@@ -196,20 +225,19 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
         const long long Np = b.Npad;
         const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
         Acc<R> acc(I.W0);
-        for (int k = 0; k < n; ++k) {
-            const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
-            if (e & NB_FAR) continue;
+        for_each_entry(b.nbr + s, Np, n, A, nullptr, [&](int, uint32_t e, const decltype(Ai) &Aj, double) {
+            if (e & NB_FAR) return;
             R rx, ry, rz, r2;
-            if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
+            if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, (int)e, rx, ry, rz, r2)) return;
             if (want_close && r2 <= close_r2) {
-                const int tj = mir_type(A[e]);
+                const int tj = mir_type(Aj);
                 close |= (tj == T_FLUID || tj == T_RIGID);
             }
             // float: correctly rounded sqrt; double: r2 / sqrt via rsqrt (~1 ulp)
             const R q = (sizeof(R) == 4 ? sqrt(r2) : r2 * rsqrt_<R>(r2)) * irc;
             const R om = lt_nonneg(q, R(1)) ? R(1) - q : R(0);
             acc.add(Wc * (R(1) + R(3) * q) * om * om * om);
-        }
+        });
         d = I.Cn * acc.value();
     }
     const double rho = I.mf * d;
@@ -227,10 +255,12 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
 // FP64 density with each unordered pair evaluated once (Newton 3): phase 1
 // sums W over the owned prefix of the list and stores each W for the partner
 // (negated when the pair lies inside the collision radius of the artificial
-// viscosity; 0 for pairs beyond h) in the pair buffer, which is free between
-// force passes; phase 2 adds the partners' values read through the reverse
-// index.  The partner's r_ji = -r_ij bit for bit and the terms are summed in
-// list order ([owned][not owned]) as in k_density, so the result is the same.
+// viscosity; 0 for pairs beyond h) in the partner's column of the pair
+// buffer, which is free between force passes (a scattered store, which does
+// not stall the thread); phase 2 reads its own column in entry order
+// (coalesced).  The partner's r_ji = -r_ij bit for bit and the terms are
+// summed in list order ([owned][not owned]) as in k_density, so the result is
+// the same.
 __device__ __forceinline__ void density_half_slot(const Bufs &b, long long s)
 {
     if (s >= b.N) return;
@@ -243,22 +273,22 @@ __device__ __forceinline__ void density_half_slot(const Bufs &b, long long s)
     const int nf = b.nfirst[s];
     const long long Np = b.Npad;
     double *__restrict__ wb = (double *)b.resB;
+    const uint16_t *__restrict__ rv = b.rev + s;
     const double close_r2 = (double)(I.artvis_r2f_hi * 1.0001f);
     const bool want_close = I.artvis != 0;
     bool close = false;
     double acc = I.W0;
-    for (int k = 0; k < nf; ++k) {
-        const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
+    for_each_entry(b.nbr + s, Np, nf, A, nullptr, [&](int k, uint32_t e, const double4_32a &Aj, double) {
         double W = 0.0;
         if (!(e & NB_FAR)) {
             double rx, ry, rz, r2;
-            if (Rel<double>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) {
+            if (Rel<double>::get(b, I, geo, Ai, Aj, gi, (int)e, rx, ry, rz, r2)) {
                 const double q = r2 * rsqrt_<double>(r2) * K<double>::inv_rc(I);
                 const double om = lt_nonneg(q, 1.0) ? 1.0 - q : 0.0;
                 W = K<double>::Wc(I) * (1.0 + 3.0 * q) * om * om * om;
                 acc = __dadd_rn(acc, W);
                 if (want_close && r2 <= close_r2) {
-                    const int tj = mir_type(A[e]);
+                    const int tj = mir_type(Aj);
                     const bool mob = (tj == T_FLUID || tj == T_RIGID);
                     if (mob && (ti == T_FLUID || ti == T_RIGID)) {
                         close = true;
@@ -267,8 +297,10 @@ __device__ __forceinline__ void density_half_slot(const Bufs &b, long long s)
                 }
             }
         }
-        wb[(long long)k * Np + s] = W;
-    }
+        // into the partner's column, at the row of its entry for this pair
+        const int row = __ldg(rv + (long long)k * Np);
+        if (row < b.capown) wb[(long long)row * Np + (e & ~NB_FAR)] = W;
+    });
     b.sd[s] = acc;   // partial; completed by k_density_gather
     b.aclose[s] = close ? 1 : 0;
 }
@@ -296,19 +328,22 @@ __global__ void __launch_bounds__(256) k_density_gather(Bufs b, int any_filter, 
         const double *__restrict__ wb = (const double *)b.resB;
         const int n = b.ncnt[s], nf = b.nfirst[s];
         const long long Np = b.Npad;
-        const uint16_t *__restrict__ rv = b.rev + s;
+        // the owners wrote W of this particle's non-owned entries into its
+        // own column (row k - nf; more rows than capown only after a list
+        // error, flagged)
+        const int nend = min(n, nf + b.capown);
         double acc = b.sd[s];
         bool close = b.aclose[s] != 0;
         constexpr int G = 4;
-        for (int k0 = nf; k0 < n; k0 += G) {
+        for (int k0 = nf; k0 < nend; k0 += G) {
             double w[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 const int k = k0 + g;
                 w[g] = 0.0;
-                if (k < n) {
+                if (k < nend) {
                     const uint32_t e = (uint32_t)__ldg(b.nbr + (long long)k * Np + s);
-                    if (!(e & NB_FAR)) w[g] = wb[(long long)__ldg(rv + (long long)k * Np) * Np + e];
+                    if (!(e & NB_FAR)) w[g] = wb[(long long)(k - nf) * Np + s];
                 }
             }
 #pragma unroll
@@ -356,17 +391,16 @@ __global__ void __launch_bounds__(256) k_reinit(Bufs b, int any_filter, const in
         const long long Np = b.Npad;
         const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
         Acc<R> num(I.W0), den(I.W0 / di);
-        for (int k = 0; k < n; ++k) {
-            const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
-            if (e & NB_FAR) continue;
+        for_each_entry(b.nbr + s, Np, n, A, b.sd, [&](int, uint32_t e, const decltype(Ai) &Aj, double dj) {
+            if (e & NB_FAR) return;
             R rx, ry, rz, r2;
-            if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
+            if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, (int)e, rx, ry, rz, r2)) return;
             const R q = sqrt(r2) * irc;
             const R om = lt_nonneg(q, R(1)) ? R(1) - q : R(0);
             const R W = Wc * (R(1) + R(3) * q) * om * om * om;
             num.add(W);
-            den.add(W / (R)b.sd[e]);
-        }
+            den.add(W / (R)dj);
+        });
         d = num.value() / den.value();
     }
     const double rho = I.mf * d;
@@ -406,17 +440,16 @@ __global__ void __launch_bounds__(256) k_filter(Bufs b, const int *gate)
         const long long Np = b.Npad;
         const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
         Acc<R> num(pi * I.W0), den(I.W0);
-        for (int k = 0; k < n; ++k) {
-            const uint32_t e = (uint32_t)b.nbr[(long long)k * Np + s];
-            if (e & NB_FAR) continue;
+        for_each_entry(b.nbr + s, Np, n, A, b.sp, [&](int, uint32_t e, const decltype(Ai) &Aj, double pj) {
+            if (e & NB_FAR) return;
             R rx, ry, rz, r2;
-            if (!Rel<R>::get(b, I, geo, Ai, A[e], gi, (int)e, rx, ry, rz, r2)) continue;
+            if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, (int)e, rx, ry, rz, r2)) return;
             const R q = sqrt(r2) * irc;
             const R om = lt_nonneg(q, R(1)) ? R(1) - q : R(0);
             const R W = Wc * (R(1) + R(3) * q) * om * om * om;
-            num.add((R)b.sp[e] * W);
+            num.add((R)pj * W);
             den.add(W);
-        }
+        });
         pf = num.value() / den.value();
     }
     b.sp2[s] = pf;
@@ -609,6 +642,15 @@ template <class R> struct PairK {
 };
 
 
+// Correctly rounded operations in precision R that the compiler may not
+// contract or reorder.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class R> struct Z6 {
     R z0, z1, z2, z3, z4, z5;
 };
@@ -669,18 +711,21 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R
     ox += c3 * (ry * wz - rz * wy);
     oy += c3 * (rz * wx - rx * wz);
     oz += c3 * (rx * wy - ry * wx);
-    // Eq. FijT: (sa S + (sb - sa) tr(S)/3 1) . e / sqrt(dt)
+    // Eq. FijT: (sa S + (sb - sa) tr(S)/3 1) . e / sqrt(dt).  Every operation
+    // on the normals is spelled out (no contraction left to the compiler), so
+    // normals drawn here and normals read back from the cache give the same
+    // force bits.
     if (P.noise) {
         if (zmode == 0)
             pair_normals<R>(mir_gid(Di), mir_gid(Dj), P.step, P.key0, P.key1, z.z0, z.z1, z.z2, z.z3,
                             z.z4, z.z5);
         const R rs = om * Di.z * Dj.z;
         const R sa = P.T1 * rs;
-        const R sxy = z.z3 * is2, sxz = z.z4 * is2, syz = z.z5 * is2;
-        ce += P.T3 * rs * (z.z0 + z.z1 + z.z2);
-        ox += sa * (z.z0 * ex + sxy * ey + sxz * ez);
-        oy += sa * (sxy * ex + z.z1 * ey + syz * ez);
-        oz += sa * (sxz * ex + syz * ey + z.z2 * ez);
+        const R sxy = mul_rn(z.z3, is2), sxz = mul_rn(z.z4, is2), syz = mul_rn(z.z5, is2);
+        ce = fma_rn(P.T3 * rs, add_rn(add_rn(z.z0, z.z1), z.z2), ce);
+        ox = fma_rn(sa, fma_rn(sxz, ez, fma_rn(sxy, ey, mul_rn(z.z0, ex))), ox);
+        oy = fma_rn(sa, fma_rn(syz, ez, fma_rn(z.z1, ey, mul_rn(sxy, ex))), oy);
+        oz = fma_rn(sa, fma_rn(z.z2, ez, fma_rn(syz, ey, mul_rn(sxz, ex))), oz);
     }
 }
 
@@ -700,16 +745,37 @@ __device__ __forceinline__ void write_fluid_force(const Bufs &b, const Inst &I, 
     b.T[3 * gi + 2] = -(double)(lev * tz);
 }
 
-// Direct (owner-computes-all) force pass over the neighbour list of fluid
-// particle i; the next neighbour's records are fetched before the current
-// pair is evaluated.
+// Fluid particle i and a rigid neighbour j (Section 2.4): Eqs. FijC and FijD
+// on i (no rotational or random part) and the drag reaction Eq.
+// F_fpi_DG_reac, added to i's sums; nothing beyond h.
+template <class R, class T4>
+__device__ __forceinline__ void fluid_rigid_pair(const Bufs &b, const Inst &I, const Geo<R> &geo,
+                                                 const PairK<R> &P, int gi, const T4 &Ai, const T4 &Bi,
+                                                 const T4 &Ci, const T4 &Di, int j, const T4 &Aj,
+                                                 const T4 &Bj, const T4 &Cj, const T4 &Dj, R &fx, R &fy,
+                                                 R &fz, R &tx, R &ty, R &tz)
+{
+    R rx, ry, rz, r2;
+    if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) return;
+    R ox, oy, oz, ce, ex, ey, ez, q, om;
+    Z6<R> z;
+    sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, false, 0, z, ox, oy, oz, ce, ex, ey, ez, q, om);
+    const double4_32a rc = b.rxn[j];
+    const R W = P.Wc * (R(1) + R(3) * q) * om * om * om;
+    fx += ox + ce * ex - (R)rc.x * W;
+    fy += oy + ce * ey - (R)rc.y * W;
+    fz += oz + ce * ez - (R)rc.z * W;
+    tx += ey * oz - ez * oy;
+    ty += ez * ox - ex * oz;
+    tz += ex * oy - ey * ox;
+}
+
+// The same, called out of line where rigid neighbours are rare and the
+// caller's registers matter (the gather), loading the records itself.
 template <class R>
-__device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s)
+__device__ __noinline__ void fluid_rigid_pair_call(const Bufs &b, long long s, int gi, int j, R *f)
 {
     using T4 = typename Vec<R>::T4;
-    if (s >= b.N) return;
-    if (b.stype[s] != T_FLUID) return;
-    const int gi = b.perm[s];
     const Inst &I = b.inst[b.pinst[gi]];
     const Geo<R> geo(I);
     const PairK<R> P(I, (uint32_t)(*b.step));
@@ -717,28 +783,92 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s)
     const T4 *__restrict__ Bm = Mir<R>::B(b);
     const T4 *__restrict__ Cm = Mir<R>::C(b);
     const T4 *__restrict__ Dm = Mir<R>::D(b);
+    fluid_rigid_pair<R>(b, I, geo, P, gi, A[s], Bm[s], Cm[s], Dm[s], j, A[j], Bm[j], Cm[j], Dm[j], f[0], f[1],
+                        f[2], f[3], f[4], f[5]);
+}
+
+// Direct (owner-computes-all) force pass over the neighbour list of fluid
+// particle i.  The index two entries ahead and the records of the next
+// neighbour are fetched before the current pair is evaluated.  With the
+// cache on, the first evaluation of a step (FILL) stores the six normals of
+// every entry in its own column (a NaN marker for an entry beyond h); the
+// second (REUSE, when the list has not been rebuilt in between) reads them
+// back, fetched one entry ahead like the records, instead of drawing them
+// again (same counter, so the same bits).
+template <class R, bool REUSE>
+__device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uint32_t step, bool fill)
+{
+    using T4 = typename Vec<R>::T4;
+    using T2 = typename Vec2<R>::T2;
+    if (s >= b.N) return;
+    if (b.stype[s] != T_FLUID) return;
+    const int gi = b.perm[s];
+    const Inst &I = b.inst[b.pinst[gi]];
+    const Geo<R> geo(I);
+    const PairK<R> P(I, step);
+    fill = fill && P.noise;
+    const T4 *__restrict__ A = Mir<R>::A(b);
+    const T4 *__restrict__ Bm = Mir<R>::B(b);
+    const T4 *__restrict__ Cm = Mir<R>::C(b);
+    const T4 *__restrict__ Dm = Mir<R>::D(b);
     const double4_32a *__restrict__ rxn = b.rxn;
+    T4 *__restrict__ zA = (T4 *)b.zdA;
+    T2 *__restrict__ zB = (T2 *)b.zdB;
     const int *__restrict__ nb = b.nbr + s;
     const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
     R fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0;
     const int n = b.ncnt[s];
     const long long Np = b.Npad;
     int jn = n > 0 ? __ldg(nb) : 0;
+    int jnn = n > 1 ? __ldg(nb + Np) : 0;
     T4 An = A[jn], Bn = Bm[jn], Cn = Cm[jn], Dn = Dm[jn];
+    T4 zan;
+    T2 zbn;
+    if (REUSE && P.noise && n > 0) { zan = zA[s]; zbn = zB[s]; }
     for (int k = 0; k < n; ++k) {
         const int j = jn;
         const T4 Aj = An, Bj = Bn, Cj = Cn, Dj = Dn;
+        T4 za;
+        T2 zb;
+        if (REUSE) { za = zan; zb = zbn; }
         if (k + 1 < n) {
-            jn = __ldg(nb + (long long)(k + 1) * Np);
+            jn = jnn;
             An = A[jn]; Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn];
+            if (REUSE && P.noise) {
+                zan = zA[(long long)(k + 1) * Np + s];
+                zbn = zB[(long long)(k + 1) * Np + s];
+            }
+            if (k + 2 < n) jnn = __ldg(nb + (long long)(k + 2) * Np);
         }
-        R rx, ry, rz, r2;
-        if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) continue;
         const bool rig = mir_type(Aj) == T_RIGID;
+        const long long at = (long long)k * Np + s;
+        R rx, ry, rz, r2;
+        if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) {
+            if (!REUSE && fill && !rig) {
+                T4 nm;
+                nm.x = R(NAN); nm.y = R(0); nm.z = R(0); nm.w = R(0);
+                zA[at] = nm;
+            }
+            continue;
+        }
         R ox, oy, oz, ce, ex, ey, ez, q, om;
         Z6<R> z;
-        sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, !rig, 0, z, ox, oy, oz, ce, ex, ey, ez,
+        int zmode = 0;
+        // an entry beyond h in the first evaluation carries the NaN marker
+        if (REUSE && P.noise && !rig && !isnan(za.x)) {
+            z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
+            zmode = 1;
+        }
+        sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, !rig, zmode, z, ox, oy, oz, ce, ex, ey, ez,
                      q, om);
+        if (!REUSE && fill && !rig) {
+            T4 zw;
+            zw.x = z.z0; zw.y = z.z1; zw.z = z.z2; zw.w = z.z3;
+            T2 zv;
+            zv.x = z.z4; zv.y = z.z5;
+            zA[at] = zw;
+            zB[at] = zv;
+        }
         if (rig) {
             // Eq. F_fpi_DG_reac: -F^DG_s W_sj / S_s
             const double4_32a rc = rxn[j];
@@ -758,25 +888,43 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s)
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_force_fluid(Bufs b)
+__global__ void __launch_bounds__(256) k_force_fluid(Bufs b, int velver)
 {
-    for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-        force_fluid_slot<R>(b, base + (threadIdx.x & 31));
+    const uint32_t step = (uint32_t)(*b.step);
+    const bool fill = b.use_cache && velver == 1;
+    const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
+                       *b.cache_step == *b.step;
+    // every warp reads the epochs before the first one is written below
+    __syncthreads();
+    if (fill && blockIdx.x == 0 && threadIdx.x == 0) {
+        *b.cache_epoch = *b.list_epoch;
+        *b.cache_step = *b.step;
+    }
+    // reuse is uniform over the launch
+    if (reuse) {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_fluid_slot<R, true>(b, base + (threadIdx.x & 31), step, false);
+    } else {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_fluid_slot<R, false>(b, base + (threadIdx.x & 31), step, fill);
+    }
 }
 
 // Newton-3 force pass, phase 1: every fluid or wall particle evaluates the
 // pairs of its owned prefix (see k_neighbors; within h, both non-rigid, at
-// least one fluid) once, stores (f, e x o) in its own column of the pair
-// buffer (coalesced) and keeps its own sum.  Each unordered pair is
+// least one fluid) once, stores (f, e x o) in the partner's column of the
+// pair buffer (at the row of the partner's entry for the pair, from k_rev)
+// and keeps its own sum.  Each unordered pair is
 // computed once instead of twice.  The first evaluation of a step stores the
-// six normals of each pair; the second reads them back when the list has not
-// been rebuilt in between (same counter, so the same bits).
-template <class R>
-__device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint32_t step, bool fill,
-                                                bool reuse)
+// six normals of each pair; the second reads them back, fetched one entry
+// ahead like the records, when the list has not been rebuilt in between (same
+// counter, so the same bits).
+template <class R, bool REUSE>
+__device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint32_t step, bool fill)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
+    constexpr bool PUSH = sizeof(R) == 8;
     if (s >= b.N) return;
     const int ti = b.stype[s];
     if (ti == T_RIGID) return;
@@ -793,52 +941,77 @@ __device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint
     T4 *__restrict__ zA = (T4 *)b.zA;
     T2 *__restrict__ zB = (T2 *)b.zB;
     const int *__restrict__ nb = b.nbr + s;
+    const uint16_t *__restrict__ rv = b.rev + s;
     const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
     const bool fi = (ti == T_FLUID);
     R fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0;
     const int last = b.nfirst[s];  // the owned prefix of the list
     const long long Np = b.Npad;
+    const bool noise = P.noise;
     int jn = 0 < last ? __ldg(nb) : 0;
+    int jnn = 1 < last ? __ldg(nb + Np) : 0;
     T4 An = A[jn], Bn = Bm[jn], Cn = Cm[jn], Dn = Dm[jn];
+    T4 zan;
+    T2 zbn;
+    if (REUSE && noise && last > 0) { zan = zA[s]; zbn = zB[s]; }
     for (int k = 0; k < last; ++k) {
         const int j = jn;
         const T4 Aj = An, Bj = Bn, Cj = Cn, Dj = Dn;
+        T4 za;
+        T2 zb;
+        if (REUSE) { za = zan; zb = zbn; }
         if (k + 1 < last) {
-            jn = __ldg(nb + (long long)(k + 1) * Np);
+            jn = jnn;
             An = A[jn]; Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn];
+            if (REUSE && noise) {
+                zan = zA[(long long)(k + 1) * Np + s];
+                zbn = zB[(long long)(k + 1) * Np + s];
+            }
+            if (k + 2 < last) jnn = __ldg(nb + (long long)(k + 2) * Np);
         }
         const int tj = mir_type(Aj);
-        if (tj == T_RIGID || (!fi && tj != T_FLUID)) continue;
-        const long long at = (long long)k * Np + s;
+        if (tj == T_RIGID) {
+            if (fi) fluid_rigid_pair<R>(b, I, geo, P, gi, Ai, Bi, Ci, Di, j, Aj, Bj, Cj, Dj, fx, fy, fz, tx,
+                                        ty, tz);
+            continue;
+        }
+        if (!fi && tj != T_FLUID) continue;
+        const long long at = (long long)k * Np + s;   // own column: normals cache
+        // FP64 results go to the partner's column, at the row of its entry
+        // for this pair (from k_rev); split results stay in the own column
+        long long pt = at;
+        bool put = true;
+        if constexpr (PUSH) {
+            const int row = __ldg(rv + (long long)k * Np);
+            put = row < b.capown;   // false only after a list error (flagged)
+            pt = (long long)row * Np + j;
+        }
         R rx, ry, rz, r2;
         if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) {
             // beyond h: marked for the partner's gather and the normals cache
             T4 nm;
             nm.x = R(NAN); nm.y = R(0); nm.z = R(0); nm.w = R(0);
-            resA[at] = nm;
-            if (fill) zA[at] = nm;
+            if (put) resA[pt] = nm;
+            if (!REUSE && fill) zA[at] = nm;
             continue;
         }
         Z6<R> z;
         int zmode = 0;
-        if (reuse && P.noise) {
-            const T4 za = zA[at];
-            if (!isnan(za.x)) {
-                const T2 zb = zB[at];
-                z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
-                zmode = 1;
-            }
+        // an entry beyond h in the first evaluation carries the NaN marker
+        if (REUSE && noise && !isnan(za.x)) {
+            z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
+            zmode = 1;
         }
         R ox, oy, oz, ce, ex, ey, ez, q, om;
         sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, true, zmode, z, ox, oy, oz, ce, ex, ey,
                      ez, q, om);
-        if (fill && P.noise) {
-            T4 za;
-            za.x = z.z0; za.y = z.z1; za.z = z.z2; za.w = z.z3;
-            T2 zb;
-            zb.x = z.z4; zb.y = z.z5;
-            zA[at] = za;
-            zB[at] = zb;
+        if (!REUSE && fill && noise) {
+            T4 zw;
+            zw.x = z.z0; zw.y = z.z1; zw.z = z.z2; zw.w = z.z3;
+            T2 zv;
+            zv.x = z.z4; zv.y = z.z5;
+            zA[at] = zw;
+            zB[at] = zv;
         }
         R gx, gy, gz, hx, hy, hz;
         pair_fh(ox, oy, oz, ce, ex, ey, ez, gx, gy, gz, hx, hy, hz);
@@ -850,9 +1023,9 @@ __device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint
             ra.x = gx; ra.y = gy; ra.z = gz; ra.w = hx;
             T2 rb;
             rb.x = hy; rb.y = hz;
-            resB[at] = rb;
+            if (put) resB[pt] = rb;
         }
-        resA[at] = ra;
+        if (put) resA[pt] = ra;
         fx += gx; fy += gy; fz += gz;
         tx += hx; ty += hy; tz += hz;
     }
@@ -866,8 +1039,9 @@ __device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint
     }
 }
 
+// (FP32: at most 128 registers, so four 128-thread blocks fit on an SM)
 template <class R>
-__global__ void __launch_bounds__(256) k_force_half(Bufs b, int velver)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_force_half(Bufs b, int velver)
 {
     const uint32_t step = (uint32_t)(*b.step);
     const bool fill = b.use_cache && velver == 1;
@@ -879,21 +1053,29 @@ __global__ void __launch_bounds__(256) k_force_half(Bufs b, int velver)
         *b.cache_epoch = *b.list_epoch;
         *b.cache_step = *b.step;
     }
-    for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-        force_half_slot<R>(b, base + (threadIdx.x & 31), step, fill, reuse);
+    // reuse is uniform over the launch
+    if (reuse) {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_half_slot<R, true>(b, base + (threadIdx.x & 31), step, false);
+    } else {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_half_slot<R, false>(b, base + (threadIdx.x & 31), step, fill);
+    }
 }
 
-// Newton-3 force pass, phase 2 (fluid particles): own sum + the stored
-// results of the pairs its partners own (read through the reverse
-// index; force negated, e x o equal; pairs the owner found beyond h carry a
-// NaN marker) + the pairs with rigid neighbours
-// evaluated directly (Eqs. FijC, FijD and the drag reaction Eq.
-// F_fpi_DG_reac) + external force.
+// Newton-3 force pass, phase 2 (fluid particles): own sum + the results of
+// the pairs its partners own (force negated, e x o equal; pairs the owner
+// found beyond h carry a NaN marker) + the pairs with rigid neighbours among
+// the non-owned entries, evaluated here (Eqs. FijC, FijD and the drag
+// reaction Eq. F_fpi_DG_reac), all in entry order + external force.  FP64
+// results were written into this particle's column (read coalesced); split
+// results are read from the owner's column through the reverse index.
 template <class R>
 __global__ void __launch_bounds__(256) k_force_gather(Bufs b)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
+    constexpr bool PUSH = sizeof(R) == 8;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     if (b.stype[s] != T_FLUID) return;
@@ -904,6 +1086,7 @@ __global__ void __launch_bounds__(256) k_force_gather(Bufs b)
     const T4 *__restrict__ resA = (const T4 *)b.resA;
     const T2 *__restrict__ resB = (const T2 *)b.resB;
     const int *__restrict__ nb = b.nbr + s;
+    const uint16_t *__restrict__ rv = b.rev + s;
     const T4 Ai = A[s];
     const T4 oa = ((const T4 *)b.ownA)[s];
     const T2 ob = ((const T2 *)b.ownB)[s];
@@ -911,35 +1094,52 @@ __global__ void __launch_bounds__(256) k_force_gather(Bufs b)
     const int n = b.ncnt[s], first = b.nfirst[s];
     const long long Np = b.Npad;
     const bool any_rigid = b.nbflag[s] & 1;
-    const uint16_t *__restrict__ rv = b.rev + s;
+    // more non-owned entries than capown only after a list error (flagged)
+    const int nend = min(n, first + b.capown);
     constexpr int G = 4;
-    for (int k0 = first; k0 < n; k0 += G) {
+    for (int k0 = first; k0 < nend; k0 += G) {
         long long at[G];
         int pj[G];
-        bool use[G];
+        bool use[G], rig[G];
+        T4 Ap[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int k = k0 + g;
-            use[g] = k < n;
+            use[g] = k < nend;
+            rig[g] = false;
             const int i = use[g] ? __ldg(nb + (long long)k * Np) : 0;
-            if (use[g] && any_rigid) use[g] = mir_type(A[i]) != T_RIGID;
             pj[g] = i;
-            at[g] = use[g] ? (long long)__ldg(rv + (long long)k * Np) * Np + i : 0;
+            if (use[g] && (!PUSH || any_rigid)) {
+                Ap[g] = A[i];
+                rig[g] = mir_type(Ap[g]) == T_RIGID;
+            }
+            if constexpr (PUSH) at[g] = (long long)(k - first) * Np + s;
+            else at[g] = (long long)(use[g] ? __ldg(rv + (long long)k * Np) : 0) * Np + i;
         }
         T4 ra[G];
-        if constexpr (sizeof(R) == 4) {
-            T4 Ap[G];
+        T2 rb[G];
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                if (use[g]) {
-                    ra[g] = resA[at[g]];
-                    Ap[g] = A[pj[g]];
-                }
+        for (int g = 0; g < G; ++g) {
+            if (use[g] && !rig[g]) {
+                ra[g] = resA[at[g]];
+                if constexpr (PUSH) rb[g] = resB[at[g]];
             }
+        }
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                // NaN marks a pair beyond h (written by the owner)
-                if (!use[g] || isnan(ra[g].x)) continue;
+        for (int g = 0; g < G; ++g) {
+            if (!use[g]) continue;
+            if (rig[g]) {
+                R f[6] = { fx, fy, fz, tx, ty, tz };
+                fluid_rigid_pair_call<R>(b, s, gi, pj[g], f);
+                fx = f[0]; fy = f[1]; fz = f[2]; tx = f[3]; ty = f[4]; tz = f[5];
+                continue;
+            }
+            // NaN marks a pair beyond h (written by the owner)
+            if (isnan(ra[g].x)) continue;
+            if constexpr (PUSH) {
+                fx -= ra[g].x; fy -= ra[g].y; fz -= ra[g].z;
+                tx += ra[g].w; ty += rb[g].x; tz += rb[g].y;
+            } else {
                 // e of the owner = -(e seen from here), bitwise
                 R rx, ry, rz;
                 geo.disp(Ai, Ap[g], rx, ry, rz);
@@ -950,51 +1150,9 @@ __global__ void __launch_bounds__(256) k_force_gather(Bufs b)
                 fx -= gx; fy -= gy; fz -= gz;
                 tx += hx; ty += hy; tz += hz;
             }
-        } else {
-            T2 rb[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                if (use[g]) {
-                    ra[g] = resA[at[g]];
-                    rb[g] = resB[at[g]];
-                }
-            }
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                if (!use[g] || isnan(ra[g].x)) continue;
-                fx -= ra[g].x; fy -= ra[g].y; fz -= ra[g].z;
-                tx += ra[g].w; ty += rb[g].x; tz += rb[g].y;
-            }
         }
     }
-    const R lev = K<R>::lever(I);
-    if (any_rigid) {
-        const PairK<R> P(I, (uint32_t)(*b.step));
-        const T4 *__restrict__ Bm = Mir<R>::B(b);
-        const T4 *__restrict__ Cm = Mir<R>::C(b);
-        const T4 *__restrict__ Dm = Mir<R>::D(b);
-        const T4 Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
-        for (int k = 0; k < n; ++k) {
-            const int j = __ldg(nb + (long long)k * Np);
-            const T4 Aj = A[j];
-            if (mir_type(Aj) != T_RIGID) continue;
-            R rx, ry, rz, r2;
-            if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) continue;
-            R ox, oy, oz, ce, ex, ey, ez, q, om;
-            Z6<R> z;
-            sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bm[j], Cm[j], Dm[j], false, 0, z, ox, oy, oz,
-                         ce, ex, ey, ez, q, om);
-            const double4_32a rc = b.rxn[j];
-            const R W = P.Wc * (R(1) + R(3) * q) * om * om * om;
-            fx += ox + ce * ex - (R)rc.x * W;
-            fy += oy + ce * ey - (R)rc.y * W;
-            fz += oz + ce * ez - (R)rc.z * W;
-            tx += ey * oz - ez * oy;
-            ty += ez * ox - ex * oz;
-            tz += ex * oy - ey * ox;
-        }
-    }
-    write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, lev);
+    write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, K<R>::lever(I));
 }
 
 // -------------------------------------------------------- rigid force pass
@@ -1343,9 +1501,9 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
             k_force_gather<double><<<nblk(b.N, bs), bs, 0, st>>>(b);
         }
     } else if (precision == SDPD_PREC_SPLIT) {
-        k_force_fluid<float><<<persistent_grid(k_force_fluid<float>, bs, b.N), bs, 0, st>>>(b);
+        k_force_fluid<float><<<persistent_grid(k_force_fluid<float>, bs, b.N), bs, 0, st>>>(b, velver);
     } else {
-        k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b);
+        k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b, velver);
     }
     if (b.nrigid) {
         if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<b.nrigid, RB, 0, st>>>(b, velver);

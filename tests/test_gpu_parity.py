@@ -195,9 +195,28 @@ def test_skin_list_reuse_keeps_exact_pairs(precision):
     assert rel_l2(st["v"], sb["v"]) < tol
 
 
-def test_noise_cache_equals_recomputation():
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("newton3", [1, 0])
+def test_noise_cache_equals_recomputation(precision, newton3):
     # the second evaluation of a step reads the normals of the first from the
-    # cache; the direct pass recomputes them: same trajectory up to rounding
+    # cache (same counter, same bits): the trajectory equals the one that
+    # draws them again, bit for bit, in both force passes
+    case = CASES["periodic12"]
+    case = dict(case, params=dict(case["params"], kBT=4.1e-15))
+    out = []
+    for on in (1, 0):
+        sim = B.Sim(case, precision=precision)
+        sim.set_force_mode(newton3)
+        sim.set_noise_cache(on)
+        sim.step(4)
+        out.append(sim.state(density=False))
+        sim.close()
+    for k in ("x", "v", "w", "F", "N"):
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_force_modes_agree():
+    # Newton-3 half pairs and the direct pass: same trajectory up to rounding
     case = CASES["periodic12"]
     case = dict(case, params=dict(case["params"], kBT=4.1e-15))
     a = B.Sim(case, precision=B.SDPD_PREC_FP64)
