@@ -480,37 +480,30 @@ __device__ __forceinline__ double exact_disp(const double *xi, const double *xj,
     return __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
 }
 
-// The sphere kernels run one CTA of RB threads per rigid particle: the
-// threads stride over its neighbour list and the partial sums are reduced in
-// a fixed order (warp shuffles, then warps 0, 1, ... in thread 0), so the
-// result does not depend on scheduling.
+// The sphere kernels run one warp per rigid particle, RB / 32 particles per
+// block: the lanes stride over its neighbour list and the partial sums are
+// reduced by a fixed butterfly of shuffles, so the result does not depend on
+// scheduling.
 constexpr int RB = 128;
+constexpr int RPB = RB / 32;   // rigid particles per block
 
 template <int K>
-__device__ __forceinline__ void block_sum_to_t0(double (&v)[K], double (*red)[K])
+__device__ __forceinline__ void warp_sum_all(double (&v)[K])
 {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int a = 0; a < K; ++a) v[a] = warp_sum(v[a]);
-    if (lane == 0)
-        for (int a = 0; a < K; ++a) red[w][a] = v[a];
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int ww = 1; ww < RB / 32; ++ww)
-            for (int a = 0; a < K; ++a) v[a] += red[ww][a];
 }
 
-// Per rigid particle s (one CTA each, threads striding over its neighbour
-// list, order-fixed block reduction): eps_s from the rigid volumes within h
+// Per rigid particle s (one warp each, lanes striding over its neighbour
+// list, order-fixed reduction): eps_s from the rigid volumes within h
 // (s included), v_f = sum W v / sum W over fluid neighbours, drag along
 // (v_f - v_s) with the Ergun (eps <= 0.8) or Wen-Yu (eps > 0.8) coefficient in
 // the closed form that stays finite at eps -> 1 and |v_f - v_s| -> 0.
 template <class R>
 __global__ void __launch_bounds__(RB) k_drag(Bufs b)
 {
-    __shared__ double red[RB / 32][5];
-    const int r = blockIdx.x;
-    if (r >= b.nrigid) return;
+    const int r = blockIdx.x * RPB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= b.nrigid) return;   // the whole warp
     const int g = b.rigid_gid[r];
     const long long s = b.slot_of[g];
     const Inst &I = b.inst[b.pinst[g]];
@@ -527,7 +520,7 @@ __global__ void __launch_bounds__(RB) k_drag(Bufs b)
         const float4 Ai = A[s];
         const float Wc = K<float>::Wc(I), irc = K<float>::inv_rc(I);
         float Sf = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
-        for (int k = threadIdx.x; k < n; k += RB) {
+        for (int k = lane; k < n; k += 32) {
             const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
             if (e & NB_FAR) continue;
             const int j = (int)e;
@@ -551,7 +544,7 @@ __global__ void __launch_bounds__(RB) k_drag(Bufs b)
         }
         S = Sf; U0 = u0; U1 = u1; U2 = u2;
     } else
-    for (int k = threadIdx.x; k < n; k += RB) {
+    for (int k = lane; k < n; k += 32) {
         const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
         if (e & NB_FAR) continue;
         const int gj = b.perm[e];
@@ -573,8 +566,8 @@ __global__ void __launch_bounds__(RB) k_drag(Bufs b)
         }
     }
     double sums[5] = { Vsum, S, U0, U1, U2 };
-    block_sum_to_t0(sums, red);
-    if (threadIdx.x != 0) return;
+    warp_sum_all(sums);
+    if (lane != 0) return;
     Vsum = sums[0] + 4.0 / 3.0 * PI * Ri * Ri * Ri;
     S = sums[1];
     U0 = sums[2];
@@ -1251,16 +1244,14 @@ __device__ __forceinline__ void hist_put(const Bufs &b, int r, int slot, int par
 
 // Rigid particles, one warp each: pressure-gradient force from the fluid
 // neighbours (Eq. F_fpi_PG), DEM + lubrication with the rigid neighbours,
-// wall planes, drag, gravity.  Lanes stride over the neighbour list in rounds
-// of 32; new history entries go to round-major, lane-minor slots (ballot),
-// so the table is deterministic.
+// wall planes, drag, gravity.  The lanes take the neighbour list in rounds of
+// 32, each entry either a fluid pair or a rigid one; new history entries go to
+// round-major, lane-minor slots (ballot), so the table is deterministic.
 template <class R>
 __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
 {
-    __shared__ double red[RB / 32][15];
-    const int r = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (r >= b.nrigid) return;
+    const int r = blockIdx.x * RPB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= b.nrigid) return;   // the whole warp
     const int g = b.rigid_gid[r];
     const long long s = b.slot_of[g];
     const Inst &I = b.inst[b.pinst[g]];
@@ -1268,126 +1259,92 @@ __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
     const double vi[3] = { b.v[3 * g], b.v[3 * g + 1], b.v[3 * g + 2] };
     const double wi[3] = { b.w[3 * g], b.w[3 * g + 1], b.w[3 * g + 2] };
     const double Ri = b.R[g], mi = b.m[g];
-    const double di = b.sd[s], Pi = b.sp2[s] / (di * di);
+    const double di = b.sd[s];
     const bool commit = (velver == 2);
+    const long long Np = b.Npad;
     double acc[15];
 #pragma unroll
     for (int a = 0; a < 15; ++a) acc[a] = 0.0;   // pg, npg, Fdem, Tdem, Flub
+    // the fluid pairs in precision R on the mirrors, as for fluid pairs (the
+    // C + D part of the SDPD pair, the exact r < h decision of Rel), summed
+    // per lane in R; DEM and lubrication stay FP64
+    using T4 = typename Vec<R>::T4;
+    const PairK<R> P(I, 0u);
+    const Geo<R> geo(I);
+    const T4 *__restrict__ A = Mir<R>::A(b);
+    const T4 *__restrict__ Bm = Mir<R>::B(b);
+    const T4 *__restrict__ Cm = Mir<R>::C(b);
+    const T4 *__restrict__ Dm = Mir<R>::D(b);
+    const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
+    const R Rr = (R)Ri;
+    R f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
     int base = 0;
     const int n = b.ncnt[s];
-    // fluid neighbours: F^C + F^D of each pair (s, j), summed for Eq. F_fpi_PG
-    if constexpr (sizeof(R) == 4) {
-        // split precision: the pair arithmetic in FP32 on the mirrors, as
-        // for fluid pairs (the C + D part of the SDPD pair; the exact r < h
-        // decision of Rel); DEM and lubrication below stay FP64
-        const PairK<float> P(I, 0u);
-        const Geo<float> geo(I);
-        const float4 *__restrict__ A = b.A32;
-        const float4 *__restrict__ Bm = Mir<float>::B(b);
-        const float4 *__restrict__ Cm = Mir<float>::C(b);
-        const float4 *__restrict__ Dm = Mir<float>::D(b);
-        const float4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
-        const float Rf = (float)Ri;
-        float f0 = 0.f, f1 = 0.f, f2 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
-        for (int k = threadIdx.x; k < n; k += RB) {
-            const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
-            if (e & NB_FAR) continue;
-            const int j = (int)e;
-            const float4 Aj = A[j];
-            if (mir_type(Aj) != T_FLUID) continue;
-            float rx, ry, rz, r2;
-            if (!Rel<float>::get(b, I, geo, Ai, Aj, g, j, rx, ry, rz, r2)) continue;
-            Z6<float> z;
-            float ox, oy, oz, ce, ex, ey, ez, q, om;
-            sdpd_pair<float>(P, rx, ry, rz, r2, Bi, Ci, Di, Bm[j], Cm[j], Dm[j], false, 0, z, ox, oy, oz, ce,
-                             ex, ey, ez, q, om);
-            f0 += ox + ce * ex;
-            f1 += oy + ce * ey;
-            f2 += oz + ce * ez;
-            // lever -R e: (-R e) x (o + ce e) = -R e x o
-            t0 -= Rf * (ey * oz - ez * oy);
-            t1 -= Rf * (ez * ox - ex * oz);
-            t2 -= Rf * (ex * oy - ey * ox);
-        }
-        acc[0] = f0; acc[1] = f1; acc[2] = f2;
-        acc[3] = t0; acc[4] = t1; acc[5] = t2;
-    } else
-    for (int k = threadIdx.x; k < n; k += RB) {
-        const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
-        if (e & NB_FAR) continue;
-        const int j = (int)e;
-        const int gj = b.perm[j];
-        if (b.type[gj] != T_FLUID) continue;
-        const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-        double rv[3];
-        const double r2 = exact_disp(xi, xj, I, rv);
-        if (!(r2 < I.rc2)) continue;
-        const double L = sqrt(r2), iL = 1.0 / L;
-        const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
-        const double ex = rv[0] * iL, ey = rv[1] * iL, ez = rv[2] * iL;
-        const double q = L / I.rc, om = 1.0 - q;
-        const double Fk = I.Fc * om * om;
-        const double dj = b.sd[j];
-        const double fc = I.coeff_c * (Pi + b.sp2[j] / (dj * dj)) * Fk;
-        const double gf = Fk / (di * dj);
-        const double ga = I.Ca * gf, gb = I.Cb * gf;
-        const double ev = ex * vij[0] + ey * vij[1] + ez * vij[2];
-        double f[3];
-        const double e3[3] = { ex, ey, ez };
-        for (int a = 0; a < 3; ++a)
-            f[a] = fc * rv[a] + I.coeff_d * (-ga * (vij[a] + e3[a] * ev * (1.0 / 3.0)) - gb * (2.0 / 3.0) * e3[a] * ev);
-        double lev[3] = { -Ri * ex, -Ri * ey, -Ri * ez }, tq[3];
-        cross3(lev, f, tq);
-        for (int a = 0; a < 3; ++a) {
-            acc[a] += f[a];
-            acc[3 + a] += tq[a];
-        }
-    }
-    // rigid neighbours (warp 0): DEM contact with its history slot in
-    // ballot order, or lubrication
-    if (warp == 0) {
-        for (int kk = 0; kk < n; kk += 32) {
-            const int k = kk + lane;
-            bool contact = false;
-            int partner = 0;
-            double dn[3] = { 0.0, 0.0, 0.0 };
-            if (k < n) {
-                const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
-                const int j = (int)(e & ~NB_FAR);
+    // the entry of the next round is fetched one round ahead
+    uint32_t en = lane < n ? (uint32_t)__ldg(b.nbr + (long long)lane * Np + s) : 0u;
+    for (int kk = 0; kk < n; kk += 32) {
+        const int k = kk + lane;
+        bool contact = false;
+        int partner = 0;
+        double dn[3] = { 0.0, 0.0, 0.0 };
+        const uint32_t e = en;
+        if (k + 32 < n) en = (uint32_t)__ldg(b.nbr + (long long)(k + 32) * Np + s);
+        if (k < n) {
+            const int j = (int)(e & ~NB_FAR);
+            const T4 Aj = A[j];
+            const int tj = mir_type(Aj);
+            if (tj == T_FLUID && !(e & NB_FAR)) {
+                // F^C + F^D of the pair (s, j), summed for Eq. F_fpi_PG
+                R rx, ry, rz, r2;
+                if (Rel<R>::get(b, I, geo, Ai, Aj, g, j, rx, ry, rz, r2)) {
+                    Z6<R> z;
+                    R ox, oy, oz, ce, ex, ey, ez, q, om;
+                    sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bm[j], Cm[j], Dm[j], false, 0, z, ox, oy, oz, ce,
+                                 ex, ey, ez, q, om);
+                    f0 += ox + ce * ex;
+                    f1 += oy + ce * ey;
+                    f2 += oz + ce * ez;
+                    // lever -R e: (-R e) x (o + ce e) = -R e x o
+                    t0 -= Rr * (ey * oz - ez * oy);
+                    t1 -= Rr * (ez * ox - ex * oz);
+                    t2 -= Rr * (ex * oy - ey * ox);
+                }
+            } else if (tj == T_RIGID) {
+                // DEM contact with its history slot in ballot order, or lubrication
                 const int gj = b.perm[j];
-                if (b.type[gj] == T_RIGID) {
-                    const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-                    double rv[3];
-                    const double r2 = exact_disp(xi, xj, I, rv);
-                    const double L = sqrt(r2);
-                    const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
-                    const double Rj = b.R[gj];
-                    const double dsum = Ri + Rj;
-                    if (L < dsum) {
-                        const double nn[3] = { rv[0] / L, rv[1] / L, rv[2] / L };
-                        double wsR[3];
-                        for (int a = 0; a < 3; ++a) wsR[a] = Ri * wi[a] + Rj * b.w[3 * gj + a];
-                        double kn, kt, cn, ct;
-                        dem_coeffs(I, Ri, Rj, mi, b.m[gj], kn, kt, cn, ct);
-                        dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
-                        contact = true;
-                        partner = gj;
-                    } else if (r2 < I.rc2) {
-                        double gap = L - dsum;
-                        const double gmin = I.lub_gap_min * dsum;
-                        if (gap < gmin) gap = gmin;
-                        const double c = 3.0 * PI * I.eta * dsum * dsum / (8.0 * gap);
-                        for (int a = 0; a < 3; ++a) acc[12 + a] += c * (-vij[a]);
-                    }
+                const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+                double rv[3];
+                const double r2 = exact_disp(xi, xj, I, rv);
+                const double L = sqrt(r2);
+                const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
+                const double Rj = b.R[gj];
+                const double dsum = Ri + Rj;
+                if (L < dsum) {
+                    const double nn[3] = { rv[0] / L, rv[1] / L, rv[2] / L };
+                    double wsR[3];
+                    for (int a = 0; a < 3; ++a) wsR[a] = Ri * wi[a] + Rj * b.w[3 * gj + a];
+                    double kn, kt, cn, ct;
+                    dem_coeffs(I, Ri, Rj, mi, b.m[gj], kn, kt, cn, ct);
+                    dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
+                    contact = true;
+                    partner = gj;
+                } else if (r2 < I.rc2) {
+                    double gap = L - dsum;
+                    const double gmin = I.lub_gap_min * dsum;
+                    if (gap < gmin) gap = gmin;
+                    const double c = 3.0 * PI * I.eta * dsum * dsum / (8.0 * gap);
+                    for (int a = 0; a < 3; ++a) acc[12 + a] += c * (-vij[a]);
                 }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, contact);
-            if (commit && contact) hist_put(b, r, base + __popc(bal & ((1u << lane) - 1u)), partner, dn);
-            base += __popc(bal);
         }
+        const unsigned bal = __ballot_sync(0xffffffffu, contact);
+        if (commit && contact) hist_put(b, r, base + __popc(bal & ((1u << lane) - 1u)), partner, dn);
+        base += __popc(bal);
     }
-    block_sum_to_t0(acc, red);
-    if (threadIdx.x != 0) return;
+    acc[0] = f0; acc[1] = f1; acc[2] = f2;
+    acc[3] = t0; acc[4] = t1; acc[5] = t2;
+    warp_sum_all(acc);
+    if (lane != 0) return;
     // contact with the planes bounding the domain on wall axes
     for (int a = 0; a < 3; ++a) {
         if (I.periodic[a]) continue;
@@ -1482,8 +1439,9 @@ void launch_density(const Bufs &b, int precision, int dflags, int newton3, const
 void launch_drag(const Bufs &b, int precision, cudaStream_t st)
 {
     if (!b.nrigid) return;
-    if (precision == SDPD_PREC_SPLIT) k_drag<float><<<b.nrigid, RB, 0, st>>>(b);
-    else k_drag<double><<<b.nrigid, RB, 0, st>>>(b);
+    const unsigned g = nblk(b.nrigid, RPB);
+    if (precision == SDPD_PREC_SPLIT) k_drag<float><<<g, RB, 0, st>>>(b);
+    else k_drag<double><<<g, RB, 0, st>>>(b);
 }
 
 
@@ -1506,8 +1464,9 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
         k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b, velver);
     }
     if (b.nrigid) {
-        if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<b.nrigid, RB, 0, st>>>(b, velver);
-        else k_force_rigid<double><<<b.nrigid, RB, 0, st>>>(b, velver);
+        const unsigned g = nblk(b.nrigid, RPB);
+        if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<g, RB, 0, st>>>(b, velver);
+        else k_force_rigid<double><<<g, RB, 0, st>>>(b, velver);
         if (velver == 2) k_hist_copy<<<nblk(b.nrigid, 64), 64, 0, st>>>(b);
     }
 }
