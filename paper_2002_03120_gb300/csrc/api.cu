@@ -215,7 +215,7 @@ sdpd_status prepare(sdpd_ctx *c)
         I.p_end = H.begin + H.n;
         // physics constants
         const double h = p.r_c;
-        I.dx = p.dx; I.rc = h; I.rc2 = h * h; I.dt = p.dt; I.hdt = 0.5 * p.dt;
+        I.dx = p.dx; I.rc = h; I.rc2 = h * h; I.inv_rc = 1.0 / h; I.dt = p.dt; I.hdt = 0.5 * p.dt;
         I.isqrt_dt = 1.0 / std::sqrt(p.dt);
         I.Wc = 105.0 / (16.0 * PI * h * h * h);
         I.Fc = 315.0 / (4.0 * PI * h * h * h * h * h);

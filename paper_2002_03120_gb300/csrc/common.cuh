@@ -35,7 +35,7 @@ struct Inst {
     int nc[3], periodic[3];
     int cell_base, ncell;
     long long p_begin, p_end;
-    double dx, rc, rc2, dt, hdt, isqrt_dt;
+    double dx, rc, rc2, inv_rc, dt, hdt, isqrt_dt;
     double Wc, Fc, W0, Cn, mf, inv_dx3;
     double rho0, p0, alpha, beta_p;
     double Ca, Cb, eta, kBT, Ka, Kb;

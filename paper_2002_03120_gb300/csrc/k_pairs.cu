@@ -77,7 +77,7 @@ template <> struct K<float> {
     __device__ __forceinline__ static float lever(const Inst &I) { return I.lever_fluidf; }
 };
 template <> struct K<double> {
-    __device__ __forceinline__ static double inv_rc(const Inst &I) { return 1.0 / I.rc; }
+    __device__ __forceinline__ static double inv_rc(const Inst &I) { return I.inv_rc; }
     __device__ __forceinline__ static double Wc(const Inst &I) { return I.Wc; }
     __device__ __forceinline__ static double Fc(const Inst &I) { return I.Fc; }
     __device__ __forceinline__ static double W0(const Inst &I) { return I.W0; }
@@ -277,15 +277,17 @@ __device__ __forceinline__ void density_half_slot(const Bufs &b, long long s)
     const double close_r2 = (double)(I.artvis_r2f_hi * 1.0001f);
     const bool want_close = I.artvis != 0;
     bool close = false;
+    const double irc = K<double>::inv_rc(I), Wc = K<double>::Wc(I);
+    const int capown = b.capown;
     double acc = I.W0;
     for_each_entry(b.nbr + s, Np, nf, A, nullptr, [&](int k, uint32_t e, const double4_32a &Aj, double) {
         double W = 0.0;
         if (!(e & NB_FAR)) {
             double rx, ry, rz, r2;
             if (Rel<double>::get(b, I, geo, Ai, Aj, gi, (int)e, rx, ry, rz, r2)) {
-                const double q = r2 * rsqrt_<double>(r2) * K<double>::inv_rc(I);
+                const double q = r2 * rsqrt_<double>(r2) * irc;
                 const double om = lt_nonneg(q, 1.0) ? 1.0 - q : 0.0;
-                W = K<double>::Wc(I) * (1.0 + 3.0 * q) * om * om * om;
+                W = Wc * (1.0 + 3.0 * q) * om * om * om;
                 acc = __dadd_rn(acc, W);
                 if (want_close && r2 <= close_r2) {
                     const int tj = mir_type(Aj);
@@ -299,7 +301,7 @@ __device__ __forceinline__ void density_half_slot(const Bufs &b, long long s)
         }
         // into the partner's column, at the row of its entry for this pair
         const int row = __ldg(rv + (long long)k * Np);
-        if (row < b.capown) wb[(long long)row * Np + (e & ~NB_FAR)] = W;
+        if (row < capown) wb[(long long)row * Np + (e & ~NB_FAR)] = W;
     });
     b.sd[s] = acc;   // partial; completed by k_density_gather
     b.aclose[s] = close ? 1 : 0;
