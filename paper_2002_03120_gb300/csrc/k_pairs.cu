@@ -459,13 +459,6 @@ __global__ void __launch_bounds__(256) k_filter(Bufs b, const int *gate)
 }
 
 // ---------------------------------------------------------------- drag (A5)
-__device__ __forceinline__ double W_d(double r, const Inst &I)
-{
-    if (r >= I.rc) return 0.0;
-    const double q = r / I.rc, om = 1.0 - q;
-    return I.Wc * (1.0 + 3.0 * q) * om * om * om;
-}
-
 // r = x_i - x_j with the minimum image; returns the oracle's r^2 (no FMA).
 __device__ __forceinline__ double exact_disp(const double *xi, const double *xj, const Inst &I, double r[3])
 {
@@ -509,64 +502,41 @@ __global__ void __launch_bounds__(RB) k_drag(Bufs b)
     const int g = b.rigid_gid[r];
     const long long s = b.slot_of[g];
     const Inst &I = b.inst[b.pinst[g]];
-    const double xi[3] = { b.x[3 * g], b.x[3 * g + 1], b.x[3 * g + 2] };
     const double Ri = b.R[g];
     double Vsum = 0.0, S = 0.0, U0 = 0.0, U1 = 0.0, U2 = 0.0;
     const int n = b.ncnt[s];
-    if constexpr (sizeof(R) == 4) {
-        // split precision: the kernel-weighted fluid sums in FP32 on the
-        // mirrors (exact r < h decision of Rel); the volumes in FP64
-        const Geo<float> geo(I);
-        const float4 *__restrict__ A = b.A32;
-        const float4 *__restrict__ Bm = Mir<float>::B(b);
-        const float4 Ai = A[s];
-        const float Wc = K<float>::Wc(I), irc = K<float>::inv_rc(I);
-        float Sf = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
-        for (int k = lane; k < n; k += 32) {
-            const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
-            if (e & NB_FAR) continue;
-            const int j = (int)e;
-            const float4 Aj = A[j];
-            const int tj = mir_type(Aj);
-            if (tj != T_RIGID && tj != T_FLUID) continue;
-            float rx, ry, rz, r2;
-            if (!Rel<float>::get(b, I, geo, Ai, Aj, g, j, rx, ry, rz, r2)) continue;
-            if (tj == T_RIGID) {
-                const double Rj = b.R[b.perm[j]];
-                Vsum += 4.0 / 3.0 * PI * Rj * Rj * Rj;
-            } else {
-                const float q = sqrtf(r2) * irc, om = 1.f - q;
-                const float W = Wc * (1.f + 3.f * q) * om * om * om;
-                const float4 Bj = Bm[j];
-                Sf += W;
-                u0 += W * Bj.x;
-                u1 += W * Bj.y;
-                u2 += W * Bj.z;
-            }
-        }
-        S = Sf; U0 = u0; U1 = u1; U2 = u2;
-    } else
+    // the kernel-weighted fluid sums in precision R on the mirrors (the
+    // exact r < h decision of Rel), per lane in R; the volumes in FP64
+    using T4 = typename Vec<R>::T4;
+    const Geo<R> geo(I);
+    const T4 *__restrict__ A = Mir<R>::A(b);
+    const T4 *__restrict__ Bm = Mir<R>::B(b);
+    const T4 Ai = A[s];
+    const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
+    R Sr = 0, u0 = 0, u1 = 0, u2 = 0;
     for (int k = lane; k < n; k += 32) {
         const uint32_t e = (uint32_t)b.nbr[(long long)k * b.Npad + s];
         if (e & NB_FAR) continue;
-        const int gj = b.perm[e];
-        const int tj = b.type[gj];
+        const int j = (int)e;
+        const T4 Aj = A[j];
+        const int tj = mir_type(Aj);
         if (tj != T_RIGID && tj != T_FLUID) continue;
-        const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-        double rv[3];
-        const double r2 = exact_disp(xi, xj, I, rv);
-        if (!(r2 < I.rc2)) continue;
+        R rx, ry, rz, r2;
+        if (!Rel<R>::get(b, I, geo, Ai, Aj, g, j, rx, ry, rz, r2)) continue;
         if (tj == T_RIGID) {
-            const double Rj = b.R[gj];
+            const double Rj = b.R[b.perm[j]];
             Vsum += 4.0 / 3.0 * PI * Rj * Rj * Rj;
         } else {
-            const double W = W_d(sqrt(r2), I);
-            S += W;
-            U0 += W * b.v[3 * gj];
-            U1 += W * b.v[3 * gj + 1];
-            U2 += W * b.v[3 * gj + 2];
+            const R q = sqrt(r2) * irc, om = R(1) - q;
+            const R W = Wc * (R(1) + R(3) * q) * om * om * om;
+            const T4 Bj = Bm[j];
+            Sr += W;
+            u0 += W * Bj.x;
+            u1 += W * Bj.y;
+            u2 += W * Bj.z;
         }
     }
+    S = Sr; U0 = u0; U1 = u1; U2 = u2;
     double sums[5] = { Vsum, S, U0, U1, U2 };
     warp_sum_all(sums);
     if (lane != 0) return;
