@@ -327,6 +327,7 @@ sdpd_status prepare(sdpd_ctx *c)
     const size_t nr1 = b.nrigid ? (size_t)b.nrigid : 1;
     ALLOC(b.eps, nr1, true);
     ALLOC(b.fdg, 3 * nr1, true);
+    ALLOC(b.dsum, 5 * nr1, true);
     const size_t nk = nr1 * c->K;
     ALLOC(b.h_n, nr1, true);
     ALLOC(b.hn_n, nr1, true);

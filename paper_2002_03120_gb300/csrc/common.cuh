@@ -101,6 +101,7 @@ struct Bufs {
     void *ownA, *ownB;         // per slot sums of the owned pairs
     // fluid-particle interaction per rigid index
     double *eps, *fdg;         // eps [nr], drag [nr][3]
+    double *dsum;              // [nr][5] fluid sums of the drag: rigid volume, S, U
     double4_32a *rxn;              // per slot: F^DG / S_s (rigid slots only)
     // DEM history: old / new tables [nr][K]
     int *h_n, *h_part, *hn_n, *hn_part;

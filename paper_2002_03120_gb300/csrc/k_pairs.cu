@@ -490,10 +490,11 @@ __device__ __forceinline__ void warp_sum_all(double (&v)[K])
 }
 
 // Per rigid particle s (one warp each, lanes striding over its neighbour
-// list, order-fixed reduction): eps_s from the rigid volumes within h
-// (s included), v_f = sum W v / sum W over fluid neighbours, drag along
-// (v_f - v_s) with the Ergun (eps <= 0.8) or Wen-Yu (eps > 0.8) coefficient in
-// the closed form that stays finite at eps -> 1 and |v_f - v_s| -> 0.
+// list, order-fixed reduction): the rigid volume within h, sum W and
+// sum W v over fluid neighbours (Eq. fvfdef, Section 2.4); k_drag_law then forms
+// eps_s (s included), v_f = sum W v / sum W and the drag along (v_f - v_s)
+// with the Ergun (eps <= 0.8) or Wen-Yu (eps > 0.8) coefficient in the closed
+// form that stays finite at eps -> 1 and |v_f - v_s| -> 0.
 template <class R>
 __global__ void __launch_bounds__(RB) k_drag(Bufs b)
 {
@@ -502,7 +503,6 @@ __global__ void __launch_bounds__(RB) k_drag(Bufs b)
     const int g = b.rigid_gid[r];
     const long long s = b.slot_of[g];
     const Inst &I = b.inst[b.pinst[g]];
-    const double Ri = b.R[g];
     double Vsum = 0.0, S = 0.0, U0 = 0.0, U1 = 0.0, U2 = 0.0;
     const int n = b.ncnt[s];
     // the kernel-weighted fluid sums in precision R on the mirrors (the
@@ -539,13 +539,24 @@ __global__ void __launch_bounds__(RB) k_drag(Bufs b)
     S = Sr; U0 = u0; U1 = u1; U2 = u2;
     double sums[5] = { Vsum, S, U0, U1, U2 };
     warp_sum_all(sums);
-    if (lane != 0) return;
-    Vsum = sums[0] + 4.0 / 3.0 * PI * Ri * Ri * Ri;
-    S = sums[1];
-    U0 = sums[2];
-    U1 = sums[3];
-    U2 = sums[4];
-    const double U[3] = { U0, U1, U2 };
+    if (lane == 0)
+        for (int a = 0; a < 5; ++a) b.dsum[5 * r + a] = sums[a];
+}
+
+// The drag law of each rigid particle from its sums (one thread each, so the
+// FP64 power functions of many particles run side by side).
+__global__ void k_drag_law(Bufs b)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= b.nrigid) return;
+    const int g = b.rigid_gid[r];
+    const long long s = b.slot_of[g];
+    const Inst &I = b.inst[b.pinst[g]];
+    const double Ri = b.R[g];
+    const double *sums = b.dsum + 5 * r;
+    const double Vsum = sums[0] + 4.0 / 3.0 * PI * Ri * Ri * Ri;
+    const double S = sums[1];
+    const double U[3] = { sums[2], sums[3], sums[4] };
     double eps = fabs(I.Vf - Vsum) / I.Vf;
     eps = fmin(fmax(eps, I.eps_min), 1.0);
     double F[3] = { 0.0, 0.0, 0.0 };
@@ -1217,13 +1228,18 @@ __device__ __forceinline__ void hist_put(const Bufs &b, int r, int slot, int par
 // Rigid particles, one warp each: pressure-gradient force from the fluid
 // neighbours (Eq. F_fpi_PG), DEM + lubrication with the rigid neighbours,
 // wall planes, drag, gravity.  The lanes take the neighbour list in rounds of
-// 32, each entry either a fluid pair or a rigid one; new history entries go to
-// round-major, lane-minor slots (ballot), so the table is deterministic.
+// 32 for the fluid pairs and collect the rigid entries, in list order, in
+// shared memory (dynamic: RPB x cap entries); the rigid pairs then run 32 at
+// a time, so their FP64 arithmetic uses the whole warp.  New history entries
+// go to slots in list order (ballot), so the table is deterministic.
 template <class R>
 __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
 {
-    const int r = blockIdx.x * RPB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    extern __shared__ uint32_t rstage[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * RPB + warp;
     if (r >= b.nrigid) return;   // the whole warp
+    uint32_t *rl = rstage + (size_t)warp * b.cap;   // this warp's rigid entries
     const int g = b.rigid_gid[r];
     const long long s = b.slot_of[g];
     const Inst &I = b.inst[b.pinst[g]];
@@ -1250,15 +1266,14 @@ __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
     const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
     const R Rr = (R)Ri;
     R f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-    int base = 0;
     const int n = b.ncnt[s];
+    const unsigned below = (1u << lane) - 1u;
+    int nr = 0;   // rigid entries collected
     // the entry of the next round is fetched one round ahead
     uint32_t en = lane < n ? (uint32_t)__ldg(b.nbr + (long long)lane * Np + s) : 0u;
     for (int kk = 0; kk < n; kk += 32) {
         const int k = kk + lane;
-        bool contact = false;
-        int partner = 0;
-        double dn[3] = { 0.0, 0.0, 0.0 };
+        bool rig = false;
         const uint32_t e = en;
         if (k + 32 < n) en = (uint32_t)__ldg(b.nbr + (long long)(k + 32) * Np + s);
         if (k < n) {
@@ -1281,36 +1296,52 @@ __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
                     t1 -= Rr * (ez * ox - ex * oz);
                     t2 -= Rr * (ex * oy - ey * ox);
                 }
-            } else if (tj == T_RIGID) {
-                // DEM contact with its history slot in ballot order, or lubrication
-                const int gj = b.perm[j];
-                const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
-                double rv[3];
-                const double r2 = exact_disp(xi, xj, I, rv);
-                const double L = sqrt(r2);
-                const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
-                const double Rj = b.R[gj];
-                const double dsum = Ri + Rj;
-                if (L < dsum) {
-                    const double nn[3] = { rv[0] / L, rv[1] / L, rv[2] / L };
-                    double wsR[3];
-                    for (int a = 0; a < 3; ++a) wsR[a] = Ri * wi[a] + Rj * b.w[3 * gj + a];
-                    double kn, kt, cn, ct;
-                    dem_coeffs(I, Ri, Rj, mi, b.m[gj], kn, kt, cn, ct);
-                    dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
-                    contact = true;
-                    partner = gj;
-                } else if (r2 < I.rc2) {
-                    double gap = L - dsum;
-                    const double gmin = I.lub_gap_min * dsum;
-                    if (gap < gmin) gap = gmin;
-                    const double c = 3.0 * PI * I.eta * dsum * dsum / (8.0 * gap);
-                    for (int a = 0; a < 3; ++a) acc[12 + a] += c * (-vij[a]);
-                }
+            } else {
+                rig = (tj == T_RIGID);
+            }
+        }
+        const unsigned rb = __ballot_sync(0xffffffffu, rig);
+        if (rig) rl[nr + __popc(rb & below)] = e;
+        nr += __popc(rb);
+    }
+    __syncwarp();
+    // rigid neighbours: DEM contact with its history slot in list order, or
+    // lubrication
+    int base = 0;
+    for (int q0 = 0; q0 < nr; q0 += 32) {
+        const int q = q0 + lane;
+        bool contact = false;
+        int partner = 0;
+        double dn[3] = { 0.0, 0.0, 0.0 };
+        if (q < nr) {
+            const int j = (int)(rl[q] & ~NB_FAR);
+            const int gj = b.perm[j];
+            const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
+            double rv[3];
+            const double r2 = exact_disp(xi, xj, I, rv);
+            const double L = sqrt(r2);
+            const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
+            const double Rj = b.R[gj];
+            const double dsum = Ri + Rj;
+            if (L < dsum) {
+                const double nn[3] = { rv[0] / L, rv[1] / L, rv[2] / L };
+                double wsR[3];
+                for (int a = 0; a < 3; ++a) wsR[a] = Ri * wi[a] + Rj * b.w[3 * gj + a];
+                double kn, kt, cn, ct;
+                dem_coeffs(I, Ri, Rj, mi, b.m[gj], kn, kt, cn, ct);
+                dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
+                contact = true;
+                partner = gj;
+            } else if (r2 < I.rc2) {
+                double gap = L - dsum;
+                const double gmin = I.lub_gap_min * dsum;
+                if (gap < gmin) gap = gmin;
+                const double c = 3.0 * PI * I.eta * dsum * dsum / (8.0 * gap);
+                for (int a = 0; a < 3; ++a) acc[12 + a] += c * (-vij[a]);
             }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, contact);
-        if (commit && contact) hist_put(b, r, base + __popc(bal & ((1u << lane) - 1u)), partner, dn);
+        if (commit && contact) hist_put(b, r, base + __popc(bal & below), partner, dn);
         base += __popc(bal);
     }
     acc[0] = f0; acc[1] = f1; acc[2] = f2;
@@ -1414,6 +1445,7 @@ void launch_drag(const Bufs &b, int precision, cudaStream_t st)
     const unsigned g = nblk(b.nrigid, RPB);
     if (precision == SDPD_PREC_SPLIT) k_drag<float><<<g, RB, 0, st>>>(b);
     else k_drag<double><<<g, RB, 0, st>>>(b);
+    k_drag_law<<<nblk(b.nrigid, 64), 64, 0, st>>>(b);
 }
 
 
@@ -1437,8 +1469,9 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
     }
     if (b.nrigid) {
         const unsigned g = nblk(b.nrigid, RPB);
-        if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<g, RB, 0, st>>>(b, velver);
-        else k_force_rigid<double><<<g, RB, 0, st>>>(b, velver);
+        const size_t smem = (size_t)RPB * b.cap * sizeof(uint32_t);
+        if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<g, RB, smem, st>>>(b, velver);
+        else k_force_rigid<double><<<g, RB, smem, st>>>(b, velver);
         if (velver == 2) k_hist_copy<<<nblk(b.nrigid, 64), 64, 0, st>>>(b);
     }
 }
