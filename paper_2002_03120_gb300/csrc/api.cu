@@ -224,6 +224,7 @@ sdpd_status prepare(sdpd_ctx *c)
         I.mf = p.rho0 * p.dx * p.dx * p.dx;
         I.inv_dx3 = 1.0 / (p.dx * p.dx * p.dx);
         I.rho0 = p.rho0; I.p0 = p.p0; I.alpha = p.alpha; I.beta_p = p.beta_p;
+        I.alpha_int = (p.alpha >= 1.0 && p.alpha <= 32.0 && p.alpha == std::floor(p.alpha)) ? (int)p.alpha : 0;
         I.eta = p.eta; I.kBT = p.kBT;
         I.Ca = std::max(0.0, 20.0 * p.eta / 3.0 - 4.0 * p.xi);
         I.Cb = std::max(0.0, 17.0 * p.xi - 40.0 * p.eta / 3.0);
@@ -452,7 +453,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     IALLOC(b.key, N); IALLOC(b.slot_in_cell, N); IALLOC(b.tmp_perm, N); IALLOC(b.perm, N);
     IALLOC(b.slot_of, N); IALLOC(b.stype, N);
     IALLOC(b.sd, N); IALLOC(b.sp, N); IALLOC(b.sp2, N);
-    IALLOC(b.rxn, N);
+    IALLOC(b.rxn, N); IALLOC(b.rxn32, N);
     IALLOC(b.A32, N);
     if (precision == SDPD_PREC_SPLIT) {
         IALLOC(b.B32, N); IALLOC(b.C32, N); IALLOC(b.D32, N);

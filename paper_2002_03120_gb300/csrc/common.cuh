@@ -43,6 +43,7 @@ struct Inst {
     double g[3], body_amp;
     int body_axis, split_axis;
     int filter, clamp, artvis, dem_law, noise, reinit;
+    int alpha_int;             // alpha when it is an integer in [1, 32], else 0
     double artvis_rlim, artvis_e;
     double kn, kt_ratio, zeta, nu_p, E_p, mu_fric;
     double lub_gap_min, eps_min, Vf;
@@ -103,6 +104,7 @@ struct Bufs {
     double *eps, *fdg;         // eps [nr], drag [nr][3]
     double *dsum;              // [nr][5] fluid sums of the drag: rigid volume, S, U
     double4_32a *rxn;              // per slot: F^DG / S_s (rigid slots only)
+    float4 *rxn32;                 // the same in FP32 (split-precision pair kernels)
     // DEM history: old / new tables [nr][K]
     int *h_n, *h_part, *hn_n, *hn_part;
     double *h_del, *hn_del;

@@ -145,15 +145,42 @@ template <> struct Acc<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
-// Per-particle quantities the force pass reads: p/d^2, 1/d, 1/sqrt(d).
+// Eq. prtcpres: p = p0 (rho / rho0)^alpha - beta; an integer alpha (7 in
+// the paper's cases) by repeated squaring instead of the general power.
+__device__ __forceinline__ double eos_pressure(const Inst &I, double rho)
+{
+    const double x = rho / I.rho0;
+    double xa;
+    if (I.alpha_int > 0) {
+        double r = 1.0, b = x;
+        for (int e = I.alpha_int; e; e >>= 1) {
+            if (e & 1) r *= b;
+            b *= b;
+        }
+        xa = r;
+    } else {
+        xa = pow(x, I.alpha);
+    }
+    return I.p0 * xa - I.beta_p;
+}
+
+// Per-particle quantities the force pass reads: p/d^2, 1/d, 1/sqrt(d) (in
+// the precision of the pair arithmetic).
 template <class R>
 __device__ __forceinline__ void finalize_slot(const Bufs &b, long long s, double d, double p)
 {
     typename Vec<R>::T4 *D = Mir<R>::D(b);
     typename Vec<R>::T4 o = D[s];
-    o.x = (R)(p / (d * d));
-    o.y = (R)(1.0 / d);
-    o.z = (R)(1.0 / sqrt(d));
+    if constexpr (sizeof(R) == 4) {
+        const float df = (float)d;
+        o.x = (float)p / (df * df);
+        o.y = 1.0f / df;
+        o.z = rsqrtf(df);
+    } else {
+        o.x = p / (d * d);
+        o.y = 1.0 / d;
+        o.z = 1.0 / sqrt(d);
+    }
     D[s] = o;
 }
 
@@ -241,7 +268,7 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
         d = I.Cn * acc.value();
     }
     const double rho = I.mf * d;
-    double p = I.p0 * pow(rho / I.rho0, I.alpha) - I.beta_p;
+    double p = eos_pressure(I, rho);
     if (I.clamp && p < 0.0) p = 0.0;
     b.aclose[s] = close ? 1 : 0;
     b.sd[s] = d;
@@ -358,7 +385,7 @@ __global__ void __launch_bounds__(256) k_density_gather(Bufs b, int any_filter, 
         b.aclose[s] = (close && (ti == T_FLUID || ti == T_RIGID)) ? 1 : 0;
     }
     const double rho = I.mf * d;
-    double p = I.p0 * pow(rho / I.rho0, I.alpha) - I.beta_p;
+    double p = eos_pressure(I, rho);
     if (I.clamp && p < 0.0) p = 0.0;
     b.sd[s] = d;
     b.sp[s] = p;
@@ -406,7 +433,7 @@ __global__ void __launch_bounds__(256) k_reinit(Bufs b, int any_filter, const in
         d = num.value() / den.value();
     }
     const double rho = I.mf * d;
-    double p = I.p0 * pow(rho / I.rho0, I.alpha) - I.beta_p;
+    double p = eos_pressure(I, rho);
     if (I.clamp && p < 0.0) p = 0.0;
     b.sdr[s] = d;
     if (I.reinit) b.sp[s] = p;
@@ -575,8 +602,10 @@ __global__ void k_drag_law(Bufs b)
         }
         for (int a = 0; a < 3; ++a) F[a] = coef * Vs * dv[a];
         b.rxn[s] = make_double4_32a(F[0] / S, F[1] / S, F[2] / S, 0.0);
+        b.rxn32[s] = make_float4((float)(F[0] / S), (float)(F[1] / S), (float)(F[2] / S), 0.f);
     } else {
         b.rxn[s] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        b.rxn32[s] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     b.eps[r] = eps;
     b.fdg[3 * r] = F[0];
@@ -721,6 +750,18 @@ __device__ __forceinline__ void write_fluid_force(const Bufs &b, const Inst &I, 
     b.T[3 * gi + 2] = -(double)(lev * tz);
 }
 
+// F^DG_s / S_s of rigid slot j in precision R (Eq. F_fpi_DG_reac).
+__device__ __forceinline__ void rxn_of(const Bufs &b, int j, float &x, float &y, float &z)
+{
+    const float4 r = b.rxn32[j];
+    x = r.x; y = r.y; z = r.z;
+}
+__device__ __forceinline__ void rxn_of(const Bufs &b, int j, double &x, double &y, double &z)
+{
+    const double4_32a r = b.rxn[j];
+    x = r.x; y = r.y; z = r.z;
+}
+
 // Fluid particle i and a rigid neighbour j (Section 2.4): Eqs. FijC and FijD
 // on i (no rotational or random part) and the drag reaction Eq.
 // F_fpi_DG_reac, added to i's sums; nothing beyond h.
@@ -736,11 +777,12 @@ __device__ __forceinline__ void fluid_rigid_pair(const Bufs &b, const Inst &I, c
     R ox, oy, oz, ce, ex, ey, ez, q, om;
     Z6<R> z;
     sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, false, 0, z, ox, oy, oz, ce, ex, ey, ez, q, om);
-    const double4_32a rc = b.rxn[j];
+    R rcx, rcy, rcz;
+    rxn_of(b, j, rcx, rcy, rcz);
     const R W = P.Wc * (R(1) + R(3) * q) * om * om * om;
-    fx += ox + ce * ex - (R)rc.x * W;
-    fy += oy + ce * ey - (R)rc.y * W;
-    fz += oz + ce * ez - (R)rc.z * W;
+    fx += ox + ce * ex - rcx * W;
+    fy += oy + ce * ey - rcy * W;
+    fz += oz + ce * ez - rcz * W;
     tx += ey * oz - ez * oy;
     ty += ez * ox - ex * oz;
     tz += ex * oy - ey * ox;
@@ -787,7 +829,6 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
     const T4 *__restrict__ Bm = Mir<R>::B(b);
     const T4 *__restrict__ Cm = Mir<R>::C(b);
     const T4 *__restrict__ Dm = Mir<R>::D(b);
-    const double4_32a *__restrict__ rxn = b.rxn;
     T4 *__restrict__ zA = (T4 *)b.zdA;
     T2 *__restrict__ zB = (T2 *)b.zdB;
     const int *__restrict__ nb = b.nbr + s;
@@ -847,11 +888,12 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
         }
         if (rig) {
             // Eq. F_fpi_DG_reac: -F^DG_s W_sj / S_s
-            const double4_32a rc = rxn[j];
+            R rcx, rcy, rcz;
+            rxn_of(b, j, rcx, rcy, rcz);
             const R W = P.Wc * (R(1) + R(3) * q) * om * om * om;
-            fx -= (R)rc.x * W;
-            fy -= (R)rc.y * W;
-            fz -= (R)rc.z * W;
+            fx -= rcx * W;
+            fy -= rcy * W;
+            fz -= rcz * W;
         }
         fx += ox + ce * ex;
         fy += oy + ce * ey;
