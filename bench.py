@@ -469,6 +469,7 @@ def main():
     peaks = measured_peaks()
     cnt = ncu_counters()
     fp64 = args.precision == "fp64"
+    integ_cnt = ncu_counters("counters_integrate").get(f"k_integrate<{'double' if fp64 else 'float'}>", {})
     # dominant kernel: the force pass (k_force_half + k_force_gather + the
     # sphere kernel), ALU bound; algorithmic flops = 160 per unordered pair
     force_flops = FLOPS_PER_PAIR * pairs
@@ -517,9 +518,13 @@ def main():
                                 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
                        "bytes_per_particle": INTEGRATE_BYTES, "particles": main_r["mobile"],
                        "ms_per_launch": main_r["integrate_ms"],
+                       "fp64_pipe_ncu": integ_cnt.get("fp64_pipe_pct", 100.0) / 100.0 if integ_cnt else None,
                        "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json); the kernel also "
                                "keeps the cell-relative mirrors current (xl64, dsp, A32, A64: about 190 B "
-                               "more per particle), which the algorithmic bytes do not count"},
+                               "more per particle), which the algorithmic bytes do not count.  Its bound "
+                               "is the FP64 pipe, not HBM: the kicks (with the exactly rounded division), "
+                               "the drift and the mirror updates are FP64 (fp64_pipe_ncu: busy fraction "
+                               "from profiles/counters_integrate.json)"},
         "e2e": {"value": pairs * 2 / (main_r["e2e_ms"] / 1e3) * ws, "unit": UNIT,
                 "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
         "split_precision" if fp64 else "fp64_path": None if other_r is None else {
