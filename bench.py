@@ -467,7 +467,10 @@ def main():
     steps_per_s = args.steps / (t_max / 1e3)
     other_val = other_r["pairs"] * 2 * args.steps / (other_r["ms"] / 1e3) if other_r else None
     peaks = measured_peaks()
-    cnt = ncu_counters()
+    # ncu counters of the profiled kernels of this workload (the dam break's
+    # were taken at half scale, DRAM bytes scaled by the particle ratio)
+    cnt = ncu_counters({"sedimentation": "counters_sedimentation",
+                        "dambreak": "counters_dambreak"}.get(args.workload, "none"))
     fp64 = args.precision == "fp64"
     integ_cnt = ncu_counters("counters_integrate").get(f"k_integrate<{'double' if fp64 else 'float'}>", {})
     # dominant kernel: the force pass (k_force_half + k_force_gather + the
