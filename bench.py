@@ -203,6 +203,22 @@ def time_native(args, ws, rank, local):
             b.record(stream)
             b.synchronize()
             fms.append(a.elapsed_time(b))
+        # the density pass (density, EOS, and the filter or reinitialisation
+        # where the workload has them) timed alone after a list build
+        dms = []
+        for _ in range(5):
+            sim.build_cells(stream)
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.compute_density(stream)
+            b.record(stream)
+            b.synchronize()
+            dms.append(a.elapsed_time(b))
+        sim.couple_drag(stream)   # leave the stage sequence complete
+        torch.cuda.synchronize()
         # the HBM-bound update kernel alone (velocity Verlet, velver 1: kick
         # and drift; the velver-2 call also runs the collision pass)
         ims = []
@@ -239,7 +255,8 @@ def time_native(args, ws, rank, local):
             e2e_ms.append(a.elapsed_time(b))
         mobile = int(sum(int(np.sum(c["type"] <= 1)) for c in sim.cases))
         out = dict(pairs=pairs, ms=total_ms, per_step=ms, kernels=kernels,
-                   force_ms=float(np.median(fms)), e2e_ms=float(np.mean(e2e_ms)),
+                   force_ms=float(np.median(fms)), density_ms=float(np.median(dms)),
+                   e2e_ms=float(np.mean(e2e_ms)),
                    integrate_ms=float(np.median(ims)), mobile=mobile, setting=setting,
                    e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N)
         sim.close()
@@ -498,6 +515,10 @@ def main():
                    "parallelism": f"replicas x{ws}",
                    "tuning": main_r["setting"] or "defaults (newton3 1, skin 0.03, block 128)"},
         "timesteps_per_s": steps_per_s,
+        "density_pass": {"ms_per_launch": main_r["density_ms"], "pairs": pairs,
+                         "pair_evals_per_s": pairs / (main_r["density_ms"] / 1e3),
+                         "note": "density + EOS (+ filter or reinitialisation where the workload "
+                                 "has them) after a list build, L2 flushed, events on the stream"},
         "step_ms": {"min": float(np.min(main_r["per_step"])), "median": float(np.median(main_r["per_step"])),
                     "max": float(np.max(main_r["per_step"]))},
         "gpu_launches": main_r["kernels"] * args.steps,
