@@ -84,10 +84,15 @@ typedef struct {
     unsigned long long seed; /* noise seed                                          */
 } sdpd_params;
 
+/* Upper bound of max_neighbors (list positions are 16-bit; the sphere kernel
+ * stages the rigid entries of four lists in shared memory). */
+#define SDPD_MAX_NEIGHBORS 4096
+
 /* Create a context for n_instances independent instances (batched viscometer
  * sweep: one launch per stage covers all instances).  params[k] and
  * n_particles[k] describe instance k.  precision: SDPD_PREC_*.  max_neighbors:
- * capacity of each particle's neighbour list (0 = 384).  max_contacts: DEM
+ * capacity of each particle's neighbour list (0 = 384, at most
+ * SDPD_MAX_NEIGHBORS, else SDPD_E_INVALID).  max_contacts: DEM
  * contact-history slots per rigid particle (0 = 16).  Validates the parameters
  * (gamma^a, gamma^b >= 0 i.e. 40 eta/51 <= xi <= 5 eta/3; periodic axes at
  * least 3 kernel radii wide; positive dx, r_c, dt, rho0).  Allocates the

@@ -402,6 +402,9 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     *out = nullptr;
     if (!params || !n_particles || n_instances < 1) return fail(SDPD_E_INVALID, "bad instance list");
     if (precision != SDPD_PREC_FP64 && precision != SDPD_PREC_SPLIT) return fail(SDPD_E_INVALID, "bad precision");
+    if (max_neighbors < 0 || max_neighbors > SDPD_MAX_NEIGHBORS)
+        return fail(SDPD_E_INVALID, "max_neighbors must be in [0, SDPD_MAX_NEIGHBORS]");
+    if (max_contacts < 0) return fail(SDPD_E_INVALID, "negative max_contacts");
     for (int k = 0; k < n_instances; ++k) {
         if (n_particles[k] < 0) return fail(SDPD_E_INVALID, "negative particle count");
         sdpd_status s = validate(params[k], k);
@@ -519,6 +522,8 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         return cleanup(fail(SDPD_E_CUDA, "cudaMemcpy pinst"));
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup(fail(SDPD_E_CUDA, "cudaStreamCreate"));
+    if (configure_kernels(c->cap) != cudaSuccess)
+        return cleanup(fail(SDPD_E_CUDA, "kernel shared-memory configuration"));
     *out = c;
     return SDPD_OK;
 }
