@@ -84,9 +84,10 @@ typedef struct {
     unsigned long long seed; /* noise seed                                          */
 } sdpd_params;
 
-/* Upper bound of max_neighbors (list positions are 16-bit; the sphere kernel
- * stages the rigid entries of four lists in shared memory). */
-#define SDPD_MAX_NEIGHBORS 4096
+/* Upper bound of max_neighbors: the sphere kernel stages the rigid entries of
+ * four lists (4 B each) in the 48 KB of shared memory a launch gets by
+ * default; list positions are 16-bit. */
+#define SDPD_MAX_NEIGHBORS 3072
 
 /* Create a context for n_instances independent instances (batched viscometer
  * sweep: one launch per stage covers all instances).  params[k] and

@@ -21,7 +21,7 @@ STATUS = {0: "SDPD_OK", 1: "SDPD_E_INVALID", 2: "SDPD_E_CUDA", 3: "SDPD_E_OOM",
           4: "SDPD_E_CAPACITY", 5: "SDPD_E_NONFINITE", 6: "SDPD_E_DOMAIN",
           7: "SDPD_E_TIMEOUT", 8: "SDPD_E_STATE"}
 SDPD_E_INVALID = 1
-SDPD_MAX_NEIGHBORS = 4096   # include/sdpd.h
+SDPD_MAX_NEIGHBORS = 3072   # include/sdpd.h
 
 
 class SdpdError(RuntimeError):

@@ -522,8 +522,6 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
         return cleanup(fail(SDPD_E_CUDA, "cudaMemcpy pinst"));
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup(fail(SDPD_E_CUDA, "cudaStreamCreate"));
-    if (configure_kernels(c->cap) != cudaSuccess)
-        return cleanup(fail(SDPD_E_CUDA, "kernel shared-memory configuration"));
     *out = c;
     return SDPD_OK;
 }

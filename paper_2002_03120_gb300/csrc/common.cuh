@@ -364,8 +364,6 @@ void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, c
 void launch_density(const Bufs &b, int precision, int dflags, int newton3, const int *gate, cudaStream_t st);
 void launch_drag(const Bufs &b, int precision, cudaStream_t st);
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st);
-// Opt the sphere kernel into the dynamic shared memory a list capacity needs.
-cudaError_t configure_kernels(int cap);
 void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st);
 void launch_integrate(const Bufs &b, int precision, int velver, int any_artvis, cudaStream_t st);
 void launch_step_done(const Bufs &b, cudaStream_t st);

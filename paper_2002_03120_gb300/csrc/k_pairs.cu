@@ -1491,18 +1491,6 @@ void launch_drag(const Bufs &b, int precision, cudaStream_t st)
 }
 
 
-static size_t rigid_smem(int cap) { return (size_t)RPB * cap * sizeof(uint32_t); }
-
-cudaError_t configure_kernels(int cap)
-{
-    const size_t smem = rigid_smem(cap);
-    if (smem <= 48 * 1024) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_force_rigid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_force_rigid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return e;
-}
-
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st)
 {
     if (!b.N) return;
@@ -1523,7 +1511,7 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
     }
     if (b.nrigid) {
         const unsigned g = nblk(b.nrigid, RPB);
-        const size_t smem = rigid_smem(b.cap);
+        const size_t smem = (size_t)RPB * b.cap * sizeof(uint32_t);
         if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<g, RB, smem, st>>>(b, velver);
         else k_force_rigid<double><<<g, RB, smem, st>>>(b, velver);
         if (velver == 2) k_hist_copy<<<nblk(b.nrigid, 64), 64, 0, st>>>(b);

@@ -42,7 +42,7 @@ def test_neighbour_capacity_is_bounded_without_gpu():
     # validated before the device is touched: SDPD_E_INVALID, not a launch failure
     from paper_2002_03120_gb300 import cases
     case = cases.poiseuille_si(nx=4, ny=8, nz=4)
-    for bad in (-1, 4097):
+    for bad in (-1, binding.SDPD_MAX_NEIGHBORS + 1):
         with pytest.raises(binding.SdpdError) as ei:
             binding.Sim(case, max_neighbors=bad)
         assert ei.value.code == binding.SDPD_E_INVALID
