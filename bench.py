@@ -406,16 +406,26 @@ def _oracle_pairs(sim, case):
     return int(np.sum(mob[ij[:, 0]] | mob[ij[:, 1]]))
 
 
+def sources_sha(paths):
+    """First 16 hex digits of the SHA-256 of the files' bytes, concatenated in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def ncu_counters(name="counters_sedimentation"):
     """ncu counters of profiled kernels (profiles/<name>.json), used only
-    while the kernel source is the one that was profiled."""
-    import hashlib
+    while the kernel source and the headers it compiles ("sources") are the
+    ones that were profiled."""
     try:
         c = json.load(open(os.path.join(ROOT, "profiles", name + ".json")))
-        src = open(os.path.join(ROOT, c["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != c["source_sha256_16"]:
-            return {}
-        return c
+        if "sources" in c:
+            ok = sources_sha(c["sources"]) == c["sources_sha256_16"]
+        else:
+            ok = sources_sha([c["source"]]) == c["source_sha256_16"]
+        return c if ok else {}
     except Exception:
         return {}
 
