@@ -259,6 +259,12 @@ sdpd_status sdpd_graph_kernels(sdpd_ctx *ctx, long long *n_kernels);
  * cudaMalloc/cudaFree may cause.  The results equal those of
  * sdpd_build_cells + sdpd_compute_density in FP64 with the filter off, up to
  * summation order.
+ * Input domain: origin and box finite with box > 0 on every axis, dx > 0,
+ * r_c > 0 and r_c / dx <= 32; otherwise SDPD_E_INVALID before any launch.
+ * Positions on periodic axes may lie anywhere (they are folded into the
+ * box); on wall axes positions outside the box are used as given.  A
+ * particle whose position is not finite gets d = p = NaN and is nobody's
+ * neighbour; the other particles are unaffected.
  * Scratch: one file-scope __device__ array of about 2 MB (cell keys, slots,
  * counts, starts, permutation) held by every GPU that loads the library until
  * the process exits.  At most SDPD_NOALLOC_MAX_PARTICLES particles and
@@ -266,11 +272,12 @@ sdpd_status sdpd_graph_kernels(sdpd_ctx *ctx, long long *n_kernels);
  * cells, >= 3; wall axes: the box plus 2 r_c on each side); larger inputs are
  * rejected with SDPD_E_INVALID.  The first call on a device resolves the
  * array's device address (with that device current) and should come before
- * any stream capture.  Every call reuses the same array and leaves its
- * contents behind: calls whose work overlaps on the GPU (different streams,
- * different host threads) race and give wrong results; serialise them.
- * Asynchronous on `stream`; no cudaMalloc, cudaFree or allocating library
- * call is made. */
+ * any stream capture; the address is kept for the process, so the library
+ * must not be used across a device reset.  Every call reuses the same array
+ * and leaves its contents behind: calls whose work overlaps on the GPU
+ * (different streams, different host threads) race and give wrong results;
+ * serialise them.  Asynchronous on `stream`; no cudaMalloc, cudaFree or
+ * allocating library call is made. */
 sdpd_status sdpd_density_noalloc(const sdpd_params *params, long long n, const double *x,
                                  const int *type, double *d_out, double *p_out, void *stream);
 

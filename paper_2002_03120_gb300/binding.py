@@ -184,12 +184,38 @@ NOALLOC_MAX_PARTICLES = 131072
 NOALLOC_MAX_CELLS = 65536
 
 
+def _check_noalloc_args(x, type_, d_out, p_out):
+    """The arrays sdpd_density_noalloc reads and writes: CUDA tensors on one
+    device, contiguous, x float64 [n, 3], type_ int32 [n], d_out and p_out
+    float64 [n].  Raises ValueError otherwise (before any library call)."""
+    import torch
+    arrs = {"x": x, "type_": type_, "d_out": d_out, "p_out": p_out}
+    want = {"x": torch.float64, "type_": torch.int32, "d_out": torch.float64, "p_out": torch.float64}
+    for name, a in arrs.items():
+        if not isinstance(a, torch.Tensor) or not a.is_cuda:
+            raise ValueError(f"density_noalloc: {name} must be a CUDA tensor")
+        if a.dtype != want[name]:
+            raise ValueError(f"density_noalloc: {name} must be {want[name]}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"density_noalloc: {name} must be contiguous")
+    if x.dim() != 2 or x.shape[1] != 3:
+        raise ValueError(f"density_noalloc: x must be [n, 3], got {tuple(x.shape)}")
+    n = int(x.shape[0])
+    for name in ("type_", "d_out", "p_out"):
+        if tuple(arrs[name].shape) != (n,):
+            raise ValueError(f"density_noalloc: {name} must be [{n}], got {tuple(arrs[name].shape)}")
+    devs = {a.device for a in arrs.values()}
+    if len(devs) != 1:
+        raise ValueError(f"density_noalloc: all arrays must be on one device, got {sorted(map(str, devs))}")
+    return n
+
+
 def density_noalloc(params: dict, x, type_, d_out, p_out, stream=None):
     """Number density and pressure of one particle set with no device
     allocation (sdpd_density_noalloc).  x [n,3] float64, type_ [n] int32,
-    d_out / p_out [n] float64: device tensors (or device pointers)."""
+    d_out / p_out [n] float64: contiguous CUDA tensors on the current device."""
+    n = _check_noalloc_args(x, type_, d_out, p_out)
     prm = make_params(params)
-    n = int(x.shape[0])
     _check(load().sdpd_density_noalloc(C.byref(prm), n, _ptr(x), _ptr(type_), _ptr(d_out),
                                        _ptr(p_out), _stream(stream)))
 

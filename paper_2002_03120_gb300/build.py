@@ -29,12 +29,24 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libsdpd")
 
 
+def headers() -> list:
+    """Every header a translation unit may include: csrc/*.cuh, csrc/*.h and
+    include/*.h."""
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    out = []
+    for d in (CSRC, inc):
+        out += [os.path.join(d, f) for f in sorted(os.listdir(d)) if f.endswith((".cuh", ".h"))]
+    return out
+
+
 def _stale(obj: str, src: str) -> bool:
+    """An object is stale when it is missing or older than its source or any
+    header (a header edit rebuilds every unit: there are few, and they build
+    in parallel)."""
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "common.cuh"),
-            os.path.join(os.path.dirname(HERE), "include", "sdpd.h")]
-    return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(d) > t for d in [src] + headers())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:

@@ -42,10 +42,30 @@ struct Grid {
     long long n;
 };
 
+// A periodic coordinate folded into [lo, lo + box): the identity for a
+// coordinate already inside (x - 0 * box = x exactly), so in-box inputs give
+// the same displacements as the context path.
+__device__ __forceinline__ double wrap_of(double x, const Grid &G, int a)
+{
+    if (!G.periodic[a]) return x;
+    return x - G.box[a] * floor((x - G.lo[a]) / G.box[a]);
+}
+
+// Cell coordinate of a (wrapped) coordinate, clamped into the grid in double
+// before the conversion, so that a huge or non-finite value cannot index
+// outside it.  On wall axes the clamp is monotone, so two particles closer
+// than r_c still fall into the same or adjacent cells.
 __device__ __forceinline__ int cell_of(double x, const Grid &G, int a)
 {
-    int k = (int)floor((x - G.lo[a]) * G.inv_cs[a]);
-    return k < 0 ? 0 : (k >= G.nc[a] ? G.nc[a] - 1 : k);
+    const double f = floor((x - G.lo[a]) * G.inv_cs[a]);
+    if (!(f >= 0.0)) return 0;   // negative or NaN
+    if (f >= (double)(G.nc[a] - 1)) return G.nc[a] - 1;
+    return (int)f;
+}
+
+__device__ __forceinline__ bool finite3(const double *x)
+{
+    return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
 }
 
 __global__ void k_na_clear(int *scr, int ncell)
@@ -58,7 +78,8 @@ __global__ void k_na_count(int *scr, Grid G, const double *x)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G.n) return;
-    const int cx = cell_of(x[3 * i], G, 0), cy = cell_of(x[3 * i + 1], G, 1), cz = cell_of(x[3 * i + 2], G, 2);
+    const int cx = cell_of(wrap_of(x[3 * i], G, 0), G, 0), cy = cell_of(wrap_of(x[3 * i + 1], G, 1), G, 1),
+              cz = cell_of(wrap_of(x[3 * i + 2], G, 2), G, 2);
     const int key = (cz * G.nc[1] + cy) * G.nc[0] + cx;
     scr[OFF_KEY + i] = key;
     scr[OFF_SLOT + i] = atomicAdd(&scr[OFF_COUNT + key], 1);
@@ -100,11 +121,19 @@ __global__ void k_na_density(const int *scr, Grid G, const double *x, const int 
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G.n) return;
+    const double xr[3] = { x[3 * i], x[3 * i + 1], x[3 * i + 2] };
+    if (!finite3(xr)) {
+        // no density for a particle without a position; it is nobody's
+        // neighbour either (every comparison with NaN fails)
+        d_out[i] = NAN;
+        p_out[i] = NAN;
+        return;
+    }
     double d;
     if (type[i] == T_OUTER) {
         d = G.inv_dx3;
     } else {
-        const double xi[3] = { x[3 * i], x[3 * i + 1], x[3 * i + 2] };
+        const double xi[3] = { wrap_of(xr[0], G, 0), wrap_of(xr[1], G, 1), wrap_of(xr[2], G, 2) };
         const int ci[3] = { cell_of(xi[0], G, 0), cell_of(xi[1], G, 1), cell_of(xi[2], G, 2) };
         double sum = G.Wc;  // self term W(0)
         for (int oz = -1; oz <= 1; ++oz) {
@@ -125,7 +154,7 @@ __global__ void k_na_density(const int *scr, Grid G, const double *x, const int 
                         if (j == i) continue;
                         double r[3];
                         for (int a = 0; a < 3; ++a) {
-                            double t = __dsub_rn(xi[a], x[3 * (long long)j + a]);
+                            double t = __dsub_rn(xi[a], wrap_of(x[3 * (long long)j + a], G, a));
                             if (G.periodic[a]) {
                                 const double hL = 0.5 * G.box[a];
                                 if (t > hL) t = __dsub_rn(t, G.box[a]);
@@ -151,7 +180,10 @@ __global__ void k_na_density(const int *scr, Grid G, const double *x, const int 
 }
 
 // Device address of the scratch array, resolved once per device (with that
-// device current) on the first call made on it.
+// device current) on the first call made on it and kept for the process.  A
+// device reset (cudaDeviceReset, or another library resetting the primary
+// context) reloads the module and may move the array, so the library must
+// not be used across one.
 std::mutex g_mu;
 int *g_addr[64] = { nullptr };
 
@@ -189,29 +221,49 @@ extern "C" sdpd_status sdpd_density_noalloc(const sdpd_params *p, long long n, c
         g_na_err = "sdpd_density_noalloc: dx, r_c, rho0 must be > 0";
         return SDPD_E_INVALID;
     }
+    // the kernel normalisation sums W over a lattice of (2 ceil(r_c/dx) + 3)^3
+    // sites on the host
+    if (!(p->r_c / p->dx <= 32.0)) {
+        g_na_err = "sdpd_density_noalloc: r_c / dx must be finite and at most 32";
+        return SDPD_E_INVALID;
+    }
     Grid G{};
+    // every axis: a finite origin, a finite box > 0 and a finite number of
+    // cells in [1, CMAX] decided in double before any integer conversion,
+    // so that no product of cell counts can overflow or turn negative
     for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(p->origin[a]) || !std::isfinite(p->box[a]) || !(p->box[a] > 0.0) ||
+            !std::isfinite(p->r_c) || !std::isfinite(p->dx)) {
+            g_na_err = "sdpd_density_noalloc: origin, box, dx and r_c must be finite, box > 0 on every axis";
+            return SDPD_E_INVALID;
+        }
         G.box[a] = p->box[a];
         G.periodic[a] = p->periodic[a] ? 1 : 0;
+        const double ncd = G.periodic[a] ? std::floor(p->box[a] / p->r_c)
+                                         : std::ceil((p->box[a] + 4.0 * p->r_c) / p->r_c);
+        if (!std::isfinite(ncd) || ncd < (G.periodic[a] ? 3.0 : 1.0)) {
+            g_na_err = G.periodic[a] ? "sdpd_density_noalloc: periodic axis narrower than 3 r_c"
+                                     : "sdpd_density_noalloc: box / r_c is not a finite positive cell count";
+            return SDPD_E_INVALID;
+        }
+        if (ncd > (double)CMAX) {
+            g_na_err = "sdpd_density_noalloc: " + std::to_string((long long)ncd) + " cells along axis " +
+                       std::to_string(a) + " exceed the static scratch limit of " + std::to_string(CMAX);
+            return SDPD_E_INVALID;
+        }
+        G.nc[a] = (int)ncd;
         if (G.periodic[a]) {
-            const int nc = (int)std::floor(p->box[a] / p->r_c);
-            if (nc < 3) {
-                g_na_err = "sdpd_density_noalloc: periodic axis narrower than 3 r_c";
-                return SDPD_E_INVALID;
-            }
-            G.nc[a] = nc;
-            G.cs[a] = p->box[a] / nc;
+            G.cs[a] = p->box[a] / G.nc[a];
             G.lo[a] = p->origin[a];
         } else {
             // the fluid region plus two kernel radii of dummy-particle layers;
             // particles beyond are clamped into the boundary cells (still exact)
             G.cs[a] = p->r_c;
             G.lo[a] = p->origin[a] - 2.0 * p->r_c;
-            G.nc[a] = (int)std::ceil((p->box[a] + 4.0 * p->r_c) / p->r_c);
         }
         G.inv_cs[a] = 1.0 / G.cs[a];
     }
-    const long long ncell = (long long)G.nc[0] * G.nc[1] * G.nc[2];
+    const long long ncell = (long long)G.nc[0] * G.nc[1] * G.nc[2];   // each factor <= CMAX
     if (ncell > CMAX) {
         g_na_err = "sdpd_density_noalloc: " + std::to_string(ncell) + " cells exceed the static scratch limit of " +
                    std::to_string(CMAX);

@@ -46,3 +46,22 @@ def test_neighbour_capacity_is_bounded_without_gpu():
         with pytest.raises(binding.SdpdError) as ei:
             binding.Sim(case, max_neighbors=bad)
         assert ei.value.code == binding.SDPD_E_INVALID
+
+
+def test_noalloc_binding_checks_its_arrays_without_gpu():
+    # host arrays, wrong dtypes or shapes are refused before the library is
+    # called (a host pointer handed to a kernel would be an illegal address)
+    import numpy as np
+    import torch
+    from paper_2002_03120_gb300 import cases
+    case = cases.poiseuille_si(nx=4, ny=8, nz=4)
+    n = len(case["x"])
+    x = np.zeros((n, 3))
+    t = np.zeros(n, dtype=np.int32)
+    d = np.zeros(n)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        binding.density_noalloc(case["params"], x, t, d, d)
+    xt = torch.zeros((n, 3), dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        binding.density_noalloc(case["params"], xt, torch.zeros(n, dtype=torch.int32),
+                                torch.zeros(n, dtype=torch.float64), torch.zeros(n, dtype=torch.float64))
