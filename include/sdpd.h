@@ -291,6 +291,24 @@ sdpd_status sdpd_density_noalloc(const sdpd_params *params, long long n, const d
 sdpd_status sdpd_noise_normals(int precision, unsigned long long seed, int inst, unsigned step, long long n,
                                const unsigned *gi, const unsigned *gj, double *z_out);
 
+/* The counter-based generator of the random term (Eq. FijT's dW; Philox4x32-10
+ * of Salmon, Moraes, Dror and Shaw, SC'11, the stream that replaces the
+ * paper's per-pair Mersenne Twister) on the GPU, exactly as the pair kernels
+ * run it: for each k < n, the 128-bit block philox(ctr[k][0..3],
+ * key[k][0..1]) into out[k][0..3].  ctr [n][4], key [n][2], out [n][4]: host
+ * uint32 arrays.  Synchronous; needs no context.  For checking the
+ * generator against published known-answer vectors. */
+sdpd_status sdpd_philox4x32_10(long long n, const unsigned *ctr, const unsigned *key, unsigned *out);
+
+/* Measured arithmetic throughput of this GPU (a measurement utility; the
+ * paper has no counterpart): out[0] FP32 fused multiply-add rate in TFLOP/s
+ * (2 flops each), out[1] the FP64 one, out[2] 32-bit integer multiply-adds in
+ * tera-operations/s, out[3] the number of SMs.  Register-resident
+ * independent chains on every SM, timed with CUDA events at the clock the
+ * GPU runs at; these are the denominators of the pair kernels' rooflines.
+ * Synchronous, about 0.2 s; allocates a small scratch buffer. */
+sdpd_status sdpd_alu_peaks(double *out);
+
 /* Checkpoint and restart (the restart files of Section 3.1): the dynamic
  * state of all instances -- positions, velocities and angular velocities
  * [N][3] FP64 in particle order, the step counter (it keys the random

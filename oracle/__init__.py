@@ -53,14 +53,17 @@ class OrcParams(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (idempotent)."""
+    """Compile the oracle shared library (idempotent).  With OpenMP where the
+    compiler has it (the per-particle loops may then run on several threads;
+    results do not depend on their number), else without."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             os.makedirs(_BUILD, exist_ok=True)
             tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                   "-std=c99", _SRC, "-o", tmp, "-lm"]
-            subprocess.run(cmd, check=True)
+            base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
+            r = subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], capture_output=True, text=True)
+            if r.returncode != 0:
+                subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -96,6 +99,7 @@ def lib():
         L.orc_get_step.argtypes = [C.c_void_p]
         L.orc_set_state.argtypes = [C.c_void_p, dp, dp, dp]
         L.orc_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_set_fields.argtypes = [C.c_void_p, dp, dp]
         L.orc_get_component.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_get_fpi.argtypes = [C.c_void_p, dp, dp]
         L.orc_get_history.argtypes = [C.c_void_p, ip, ip, dp]
@@ -117,6 +121,8 @@ def lib():
         L.orc_profile.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.orc_overflow.argtypes = [C.c_void_p]
         L.orc_set_sample.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte)]
+        L.orc_threads.restype = C.c_int
+        L.orc_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -145,6 +151,12 @@ def make_params(p: dict) -> OrcParams:
         else:
             setattr(s, name, float(val))
     return s
+
+
+def threads(n: int = 0) -> int:
+    """Set the number of threads of the oracle's per-particle loops (n > 0)
+    and return the number in use (1 when built without OpenMP)."""
+    return int(lib().orc_threads(int(n)))
 
 
 # ---------------------------------------------------------------- pure functions
@@ -232,6 +244,7 @@ class OracleSim:
         self._h = L.orc_create(C.byref(self._P), int(inst), self.n, _dp(x), _dp(v), _dp(w),
                                _ip(t), _dp(R), _dp(m), int(K))
         self.type = t.copy()
+        self.mass = m.copy()
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -250,6 +263,12 @@ class OracleSim:
     def set_state(self, x=None, v=None, w=None):
         keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, w)]
         lib().orc_set_state(self._h, *[None if a is None else _dp(a) for a in keep])
+
+    def set_fields(self, d=None, p=None):
+        """Impose number densities and/or pressures (test hook; the force
+        routines then read these instead of those of density())."""
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (d, p)]
+        lib().orc_set_fields(self._h, *[None if a is None else _dp(a) for a in keep])
 
     def state(self):
         n = self.n
@@ -330,6 +349,71 @@ class OracleSim:
         mu = np.zeros(1)
         lib().orc_profile(self._h, int(nbins), _dp(prof), _dp(mu))
         return prof, float(mu[0])
+
+    def diagnostics(self) -> np.ndarray:
+        """Plain sums over the oracle's state (the definitions, no blocking):
+        [0..2] total momentum sum m v and [3] kinetic energy 1/2 sum m v^2 of
+        the mobile (fluid and rigid) particles, [4] their kinetic temperature
+        (sum m v^2 - |P|^2 / M) / (3 n) in energy units (the kBT of the
+        fluctuation-dissipation balance of Section 2.1 at equipartition),
+        [5] max |v| over them, [6] min and [7] max number density over all
+        but the outer walls (valid after density()), [8] the number of
+        non-finite components of x, v and w over all particles."""
+        st = self.state()
+        t = self.type
+        mob = (t == T_FLUID) | (t == T_RIGID)
+        v = st["v"][mob]
+        m = self.mass[mob]
+        out = np.zeros(16)
+        P = np.array([np.sum(m * v[:, a]) for a in range(3)])
+        v2 = np.sum(v * v, axis=1)
+        E2 = np.sum(m * v2)
+        M = np.sum(m)
+        n = int(np.sum(mob))
+        out[0:3] = P
+        out[3] = 0.5 * E2
+        out[4] = (E2 - (P @ P) / M) / (3.0 * n) if n else 0.0
+        out[5] = np.sqrt(v2.max()) if n else 0.0
+        d = st["d"][t != T_OUTER_WALL]
+        if len(d):
+            out[6] = d.min()
+            out[7] = d.max()
+        out[8] = sum(int(np.sum(~np.isfinite(st[k]))) for k in ("x", "v", "w"))
+        return out
+
+    def viscosity_fit(self, nbins: int) -> float:
+        """Viscosity from the curvature of the steady reverse-Poiseuille profile
+        (Section 4.1: the parabola of Eq. poiseuanasol fitted to the convex
+        and concave halves; reading B6): fluid particles binned into nbins
+        slabs of split_axis; per half, a least-squares parabola (numpy
+        polyfit) of the slab mean velocity along body_axis against the slab
+        mean position, over the slabs whose mean position lies at least h
+        from both ends of the half; steady state mu v'' = -rho0 a with
+        a = +body_amp on the lower half and -body_amp on the upper one; the
+        mean of the two halves."""
+        P = self.params
+        ax, fa = int(P["split_axis"]), int(P["body_axis"])
+        L, h = float(P["box"][ax]), float(P["r_c"])
+        st = self.state()
+        fl = self.type == T_FLUID
+        rel = st["x"][fl, ax] - float(P["origin"][ax])
+        u = st["v"][fl, fa]
+        b = np.clip(np.floor(rel / L * nbins).astype(np.int64), 0, nbins - 1)
+        cnt = np.bincount(b, minlength=nbins).astype(np.float64)
+        has = cnt > 0
+        vmean = np.bincount(b, weights=u, minlength=nbins)[has] / cnt[has]
+        ymean = np.bincount(b, weights=rel, minlength=nbins)[has] / cnt[has]
+        mus = []
+        for half in (0, 1):
+            y0 = half * 0.5 * L
+            y1 = y0 + 0.5 * L
+            use = (ymean >= y0 + h) & (ymean <= y1 - h)
+            if np.sum(use) < 4:
+                raise ValueError("viscosity_fit: fewer than 4 slabs h away from the ends of a half")
+            c2 = np.polyfit(ymean[use] - 0.5 * (y0 + y1), vmean[use], 2)[0]
+            a = float(P["body_amp"]) if half == 0 else -float(P["body_amp"])
+            mus.append(-float(P["rho0"]) * a / (2.0 * c2))
+        return 0.5 * (mus[0] + mus[1])
 
     def set_sample(self, idx=None):
         """Compute forces only for the particles in idx (None: all)."""

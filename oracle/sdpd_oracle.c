@@ -30,6 +30,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PI 3.14159265358979323846
 
@@ -378,6 +381,18 @@ void orc_set_state(orc_sim *s, const double *x, const double *v, const double *w
     if (w) memcpy(s->w, w, n3 * sizeof(double));
 }
 
+/* Test hook: impose number densities d and pressures p (either may be NULL)
+ * in place of those of orc_density, e.g. a hydrostatic field on a perfect
+ * lattice; rho follows as m_f d.  The force routines read them as they are. */
+void orc_set_fields(orc_sim *s, const double *d, const double *p)
+{
+    const double mf = s->P.rho0 * s->P.dx * s->P.dx * s->P.dx;
+    for (int i = 0; i < s->n; ++i) {
+        if (d) { s->d[i] = d[i]; s->rho[i] = mf * d[i]; }
+        if (p) s->p[i] = p[i];
+    }
+}
+
 void orc_get_state(const orc_sim *s, double *x, double *v, double *w, double *F, double *N,
                    double *d, double *p)
 {
@@ -426,15 +441,6 @@ void orc_set_history(orc_sim *s, const int *counts, const int *partner, const do
  * head particle per cell and a linked list through the particles (Grest et
  * al.); every particle then collects the j != i with r_ij < h from the
  * surrounding cells.  Grid cells are at least h wide. */
-static void append_nb(orc_sim *s, int j)
-{
-    if (s->nb_len >= s->nb_cap) {
-        s->nb_cap = s->nb_cap ? 2 * s->nb_cap : 1024;
-        s->nb = (int *)realloc(s->nb, (size_t)s->nb_cap * sizeof(int));
-    }
-    s->nb[s->nb_len++] = j;
-}
-
 int orc_neighbors(orc_sim *s)
 {
     const orc_params *P = &s->P;
@@ -477,43 +483,64 @@ int orc_neighbors(orc_sim *s)
         link[i] = head[c];
         head[c] = i;
     }
-    s->nb_len = 0;
+    /* two passes over the particles, each owning its own list: count, then
+     * (after a prefix sum of the counts) fill; the lists are the same as
+     * one sequential pass would append, at any number of threads */
     const double rc2 = P->r_c * P->r_c;
-    for (int i = 0; i < n; ++i) {
-        s->nb_off[i] = (int)s->nb_len;
-        /* distinct neighbour cells (a small periodic grid may wrap onto itself) */
-        long cells[27];
-        int ncl = 0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dxo = -1; dxo <= 1; ++dxo) {
-                    int off[3] = { dxo, dy, dz };
-                    int cc[3];
-                    int ok = 1;
-                    for (int a = 0; a < 3; ++a) {
-                        int k = cell_of[3 * i + a] + off[a];
-                        if (P->periodic[a]) {
-                            k = ((k % nc[a]) + nc[a]) % nc[a];
-                        } else if (k < 0 || k >= nc[a]) {
-                            ok = 0;
-                        }
-                        cc[a] = k;
-                    }
-                    if (!ok) continue;
-                    long c = ((long)cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
-                    int dup = 0;
-                    for (int q = 0; q < ncl; ++q) if (cells[q] == c) dup = 1;
-                    if (!dup) cells[ncl++] = c;
-                }
-        for (int q = 0; q < ncl; ++q) {
-            for (int j = head[cells[q]]; j >= 0; j = link[j]) {
-                if (j == i) continue;
-                double r[3];
-                double r2 = pair_vec(P, s->x + 3 * i, s->x + 3 * j, r);
-                if (r2 < rc2) append_nb(s, j);
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            long tot = 0;
+            for (int i = 0; i < n; ++i) { s->nb_off[i] = (int)tot; tot += cnt[i]; }
+            s->nb_len = tot;
+            if (tot > s->nb_cap) {
+                s->nb_cap = tot;
+                s->nb = (int *)realloc(s->nb, (size_t)s->nb_cap * sizeof(int));
             }
         }
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            /* distinct neighbour cells (a small periodic grid may wrap onto itself) */
+            long cells[27];
+            int ncl = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dxo = -1; dxo <= 1; ++dxo) {
+                        int off[3] = { dxo, dy, dz };
+                        int cc[3];
+                        int ok = 1;
+                        for (int a = 0; a < 3; ++a) {
+                            int k = cell_of[3 * i + a] + off[a];
+                            if (P->periodic[a]) {
+                                k = ((k % nc[a]) + nc[a]) % nc[a];
+                            } else if (k < 0 || k >= nc[a]) {
+                                ok = 0;
+                            }
+                            cc[a] = k;
+                        }
+                        if (!ok) continue;
+                        long c = ((long)cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+                        int dup = 0;
+                        for (int q = 0; q < ncl; ++q) if (cells[q] == c) dup = 1;
+                        if (!dup) cells[ncl++] = c;
+                    }
+            int m = 0;
+            int *out = pass ? s->nb + s->nb_off[i] : NULL;
+            for (int q = 0; q < ncl; ++q) {
+                for (int j = head[cells[q]]; j >= 0; j = link[j]) {
+                    if (j == i) continue;
+                    double r[3];
+                    double r2 = pair_vec(P, s->x + 3 * i, s->x + 3 * j, r);
+                    if (r2 < rc2) {
+                        if (out) out[m] = j;
+                        ++m;
+                    }
+                }
+            }
+            if (!pass) cnt[i] = m;
+        }
     }
+    free(cnt);
     s->nb_off[n] = (int)s->nb_len;
     free(head);
     free(link);
@@ -568,6 +595,7 @@ void orc_density(orc_sim *s)
     const double h = P->r_c;
     const double Cn = orc_kernel_norm(P->dx, h);
     const double mf = P->rho0 * P->dx * P->dx * P->dx;
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < s->n; ++i) {
         double di;
         if (s->type[i] == T_OUTER_WALL) {
@@ -603,6 +631,7 @@ void orc_reinit(orc_sim *s)
     const double h = P->r_c;
     const double mf = P->rho0 * P->dx * P->dx * P->dx;
     double *dn = (double *)malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(double));
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < s->n; ++i) {
         if (s->type[i] == T_OUTER_WALL) { dn[i] = s->d[i]; continue; }
         double w0 = orc_W(0.0, h);
@@ -637,6 +666,7 @@ void orc_filter(orc_sim *s)
     if (!P->pressure_filter) return;
     const double h = P->r_c;
     double *pn = (double *)malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(double));
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < s->n; ++i) {
         if (s->type[i] == T_OUTER_WALL) { pn[i] = s->p[i]; continue; }
         double w0 = orc_W(0.0, h);
@@ -716,6 +746,7 @@ static void sdpd_pair(const orc_sim *s, int i, int j, const double r[3], double 
 static void compute_fluid(orc_sim *s)
 {
     const orc_params *P = &s->P;
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < s->n; ++i) {
         if (s->only && !s->only[i]) continue;
         double *Fs = s->F_sdpd + 3 * i, *Ns = s->N_sdpd + 3 * i, *Fp = s->F_pg + 3 * i;
@@ -766,6 +797,7 @@ static void compute_fpi_action(orc_sim *s)
     const orc_params *P = &s->P;
     const double h = P->r_c;
     const double Vf = 4.0 / 3.0 * ORC_PI * h * h * h;
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < s->n; ++i) {
         if (s->type[i] != T_RIGID) continue;
         double Vsum = 4.0 / 3.0 * ORC_PI * s->R[i] * s->R[i] * s->R[i];
@@ -809,6 +841,7 @@ static void compute_fpi_reaction(orc_sim *s)
 {
     const orc_params *P = &s->P;
     const double h = P->r_c;
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int j = 0; j < s->n; ++j) {
         if (s->type[j] != T_FLUID) continue;
         if (s->only && !s->only[j]) continue;
@@ -925,6 +958,7 @@ static void compute_rigid(orc_sim *s, int velver)
     int *rig = (int *)malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(int));
     for (int i = 0; i < s->n; ++i)
         if (s->type[i] == T_RIGID) rig[nr++] = i;
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int ri = 0; ri < nr; ++ri) {
         const int i = rig[ri];
         if (s->only && !s->only[i]) continue;
@@ -1043,6 +1077,7 @@ void orc_update(orc_sim *s, int velver)
 {
     const orc_params *P = &s->P;
     const double hdt = 0.5 * P->dt;
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < s->n; ++i) {
         if (!is_mobile(s->type[i])) continue;
         for (int a = 0; a < 3; ++a) {
@@ -1068,6 +1103,7 @@ void orc_artvis(orc_sim *s)
     size_t n3 = (size_t)s->n * 3;
     double *dv = (double *)calloc(n3 + 1, sizeof(double));
     double rlim = P->artvis_alpha * P->dx;
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < s->n; ++i) {
         if (!is_mobile(s->type[i])) continue;
         for (int k = s->nb_off[i]; k < s->nb_off[i + 1]; ++k) {
@@ -1157,3 +1193,18 @@ void orc_profile(const orc_sim *s, int nbins, double *profile, double *mu_app)
 
 int orc_overflow(const orc_sim *s) { return s->overflow; }
 int orc_n_neighbors(const orc_sim *s, int i) { return s->nb_off[i + 1] - s->nb_off[i]; }
+
+/* Threads of the per-particle loops (OpenMP, when the oracle was built with
+ * it): every particle owns its sums and its list, so the results do not
+ * depend on the count.  n <= 0 leaves it unchanged; returns the count in
+ * use (1 without OpenMP). */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}

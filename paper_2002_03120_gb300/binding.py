@@ -76,7 +76,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
            "sdpd_set_force_mode", "sdpd_set_noise_cache", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_density_noalloc",
            "sdpd_check",
-           "sdpd_last_error", "sdpd_noise_normals", "sdpd_viscosity_fit", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
+           "sdpd_last_error", "sdpd_noise_normals", "sdpd_philox4x32_10", "sdpd_alu_peaks", "sdpd_viscosity_fit", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
            "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
 
 
@@ -132,6 +132,8 @@ def load(build_if_missing: bool = True):
         "sdpd_checkpoint": (st, [vp, vp, C.c_longlong]),
         "sdpd_restore": (st, [vp, vp, C.c_longlong]),
         "sdpd_noise_normals": (st, [C.c_int, C.c_ulonglong, C.c_int, C.c_uint, C.c_longlong, vp, vp, vp]),
+        "sdpd_philox4x32_10": (st, [C.c_longlong, vp, vp, vp]),
+        "sdpd_alu_peaks": (st, [vp]),
         "mlp_init": (st, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.POINTER(vp)]),
         "mlp_destroy": (None, [vp]),
         "mlp_param_count": (C.c_int, []),
@@ -388,6 +390,27 @@ class Sim:
 
     def check(self):
         _check(load().sdpd_check(self._h))
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Raw Philox4x32-10 blocks computed on the GPU (sdpd_philox4x32_10):
+    ctr [n, 4] and key [n, 2] uint32 -> [n, 4] uint32."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    if c.shape[0] != k.shape[0]:
+        raise ValueError("philox4x32_10: one key per counter")
+    out = np.zeros_like(c)
+    _check(load().sdpd_philox4x32_10(c.shape[0], _ptr(c), _ptr(k), _ptr(out)))
+    return out
+
+
+def alu_peaks() -> dict:
+    """Measured FP32 / FP64 FMA and INT32 IMAD throughput of the current GPU
+    (sdpd_alu_peaks)."""
+    out = np.zeros(4)
+    _check(load().sdpd_alu_peaks(_ptr(out)))
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "int32_tops": float(out[2]),
+            "sms": int(out[3])}
 
 
 def noise_normals(precision: int, seed: int, inst: int, step: int, gi, gj) -> np.ndarray:

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsdpd.so")
-SOURCES = ["api.cu", "k_cells.cu", "k_pairs.cu", "k_update.cu", "static_scratch.cu", "mlp.cu"]
+SOURCES = ["api.cu", "k_cells.cu", "k_pairs.cu", "k_update.cu", "static_scratch.cu", "mlp.cu", "k_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1157,6 +1157,27 @@ sdpd_status sdpd_noise_normals(int precision, unsigned long long seed, int inst,
     return s;
 }
 
+sdpd_status sdpd_philox4x32_10(long long n, const unsigned *ctr, const unsigned *key, unsigned *out)
+{
+    if (n < 0 || (n && (!ctr || !key || !out))) return fail(SDPD_E_INVALID, "sdpd_philox4x32_10: bad argument");
+    if (!n) return SDPD_OK;
+    (void)cudaGetLastError();
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, 10 * n * sizeof(uint32_t)) != cudaSuccess)
+        return fail(SDPD_E_OOM, "sdpd_philox4x32_10: cudaMalloc");
+    sdpd_status s = SDPD_OK;
+    if (cudaMemcpy(d, ctr, 4 * n * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d + 4 * n, key, 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = fail(SDPD_E_CUDA, "sdpd_philox4x32_10: copy in");
+    if (s == SDPD_OK) {
+        launch_philox_raw(n, d, d + 4 * n, d + 6 * n, 0);
+        if (cudaMemcpy(out, d + 6 * n, 4 * n * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            s = fail(SDPD_E_CUDA, "sdpd_philox4x32_10: kernel or copy out");
+    }
+    cudaFree(d);
+    return s;
+}
+
 sdpd_status sdpd_diagnostics(sdpd_ctx *c, int inst, double out[16])
 {
     if (!c || inst < 0 || inst >= c->n_inst || !out) return fail(SDPD_E_INVALID, "bad argument");

@@ -371,6 +371,7 @@ void launch_probe(const Bufs &b, int inst, int nbins, cudaStream_t st, long long
 void launch_diag(const Bufs &b, int inst, cudaStream_t st, long long n);
 void launch_count_pairs(const Bufs &b, cudaStream_t st);
 void launch_absorb(const Bufs &b, int precision, const double *xs, int has_x, cudaStream_t st);
+void launch_philox_raw(long long n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
 void launch_noise_normals(int precision, long long n, const uint32_t *gi, const uint32_t *gj, uint32_t step,
                           uint32_t k0, uint32_t k1, double *out, cudaStream_t st);
 

@@ -392,6 +392,26 @@ __global__ void k_noise_normals(long long n, const uint32_t *gi, const uint32_t 
     for (int k = 0; k < 6; ++k) out[6 * i + k] = (double)z[k];
 }
 
+// Raw Philox4x32-10 blocks for given counters and keys (the generator of
+// the random term, exposed so its bits can be checked against published
+// known-answer vectors).
+__global__ void k_philox_raw(long long n, const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 r = philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+void launch_philox_raw(long long n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st)
+{
+    if (n) k_philox_raw<<<nblk(n, 256), 256, 0, st>>>(n, ctr, key, out);
+}
+
 void launch_noise_normals(int precision, long long n, const uint32_t *gi, const uint32_t *gj, uint32_t step,
                           uint32_t k0, uint32_t k1, double *out, cudaStream_t st)
 {

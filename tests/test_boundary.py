@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared(header):
     src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b((?:sdpd|mlp)_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b((?:sdpd|mlp)_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():

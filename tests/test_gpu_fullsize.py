@@ -14,7 +14,7 @@ import oracle
 from paper_2002_03120_gb300 import binding as B
 from paper_2002_03120_gb300 import cases
 
-from _gpu_common import TOL_FORCE, need_gpu, rel_l2
+from _gpu_common import TOL_FORCE, check_per_type, need_gpu, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +49,8 @@ def test_dam_break_full_size_sampled_parity():
     assert rel_l2(g["d"], o["d"]) < 1e-6
     assert rel_l2(g["F"][idx], o["F"][idx]) < TOL_FORCE[B.SDPD_PREC_SPLIT]
     assert rel_l2(g["N"][idx], o["N"][idx]) < TOL_FORCE[B.SDPD_PREC_SPLIT]
+    errs = check_per_type(g, o, case["type"], TOL_FORCE[B.SDPD_PREC_SPLIT], idx)
+    assert "rigid" in errs
 
 
 def test_dam_break_full_size_steps():
@@ -87,6 +89,7 @@ def test_batched_viscometer_full_size():
         o = orc.state()
         assert rel_l2(g["d"], o["d"]) < 1e-6
         assert rel_l2(g["F"][idx], o["F"][idx]) < TOL_FORCE[B.SDPD_PREC_SPLIT]
+        check_per_type(g, o, case["type"], TOL_FORCE[B.SDPD_PREC_SPLIT], idx)
     sim.step(3)
     for k in range(len(insts)):
         assert sim.diagnostics(k)[8] == 0

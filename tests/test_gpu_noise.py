@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2002_03120_gb300 import binding as B
 
-from _gpu_common import need_gpu
+from _gpu_common import need_gpu, philox_kat
 
 pytestmark = pytest.mark.gpu
 
@@ -53,3 +53,17 @@ def test_normals_symmetric_and_keyed():
     c = B.noise_normals(B.SDPD_PREC_FP64, 9, 1, 5, gi, gj)   # another instance
     d = B.noise_normals(B.SDPD_PREC_FP64, 9, 0, 6, gi, gj)   # another step
     assert np.mean(a == c) < 1e-3 and np.mean(a == d) < 1e-3
+
+
+def test_gpu_philox_known_answer_vectors():
+    # the generator the pair kernels run, against the published vectors
+    ctr, key, want = philox_kat()
+    got = B.philox4x32_10(ctr, key)
+    assert np.array_equal(got, want)
+    # and bit for bit with the oracle over many counters and keys
+    rng = np.random.default_rng(4)
+    c = rng.integers(0, 1 << 32, size=(5000, 4), dtype=np.uint64).astype(np.uint32)
+    k = rng.integers(0, 1 << 32, size=(5000, 2), dtype=np.uint64).astype(np.uint32)
+    g = B.philox4x32_10(c, k)
+    ref = np.array([oracle.philox(a.tolist(), b.tolist()) for a, b in zip(c, k)], dtype=np.uint32)
+    assert np.array_equal(g, ref)

@@ -8,7 +8,7 @@ import oracle
 from paper_2002_03120_gb300 import binding as B
 from paper_2002_03120_gb300 import cases
 
-from _gpu_common import TOL_FORCE, need_gpu, pair_set, rel_l2
+from _gpu_common import TOL_FORCE, check_per_type, need_gpu, pair_set, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -75,6 +75,34 @@ def test_density_pressure_forces(name, precision):
     assert rel_l2(g["N"], o["N"]) < TOL_FORCE[precision]
 
 
+def _moving(case, seed):
+    """The case with random velocities and spins on its mobile particles, so
+    that every term of the pair forces (dissipative, rotational, drag,
+    lubrication) is non-zero."""
+    c = dict(case)
+    rng = np.random.default_rng(seed)
+    mob = (c["type"] <= 1)[:, None]
+    scale = 0.05 if c["params"]["dx"] == 1.0 else 1e-3
+    c["v"] = np.where(mob, rng.normal(0, scale, c["v"].shape), 0.0)
+    c["w"] = np.where(mob, rng.normal(0, scale / c["params"]["dx"], c["w"].shape), 0.0)
+    return c
+
+
+@pytest.mark.parametrize("velver", [1, 2])
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("name", ["sediment_small", "dambreak_small", "slurry_small"])
+def test_forces_per_particle_type(name, precision, velver):
+    # fluid and rigid particles judged separately (force and torque), so the
+    # few spheres' pressure-gradient force, torque, drag reaction and contact
+    # forces are held to the tolerance on their own
+    case = _moving(CASES[name], 11)
+    sim = _gpu_eval(case, precision, velver=velver, step=4)
+    orc = _oracle_eval(case, velver=velver, step=4)
+    errs = check_per_type(sim.state(), orc.state(), case["type"], TOL_FORCE[precision])
+    assert "rigid" in errs and "fluid" in errs
+    sim.close()
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_forces_velver2_with_history(precision):
     case = CASES["dambreak_small"]
@@ -114,6 +142,7 @@ def test_config2_full_size_parity():
         assert pair_set(sim.pairs()) == pair_set(orc.pairs())
         assert rel_l2(g["F"], o["F"]) < TOL_FORCE[precision]
         assert rel_l2(g["N"], o["N"]) < TOL_FORCE[precision]
+        check_per_type(g, o, case["type"], TOL_FORCE[precision])
         sim.close()
 
 

@@ -152,6 +152,33 @@ def test_lubrication_is_antisymmetric_and_dissipative():
     assert np.linalg.norm(s2.component("lub")[0]) == pytest.approx(3 * np.linalg.norm(F[0]), rel=1e-12)
 
 
+@pytest.mark.parametrize("gap_frac", [0.05, 0.2, 0.6])
+def test_lubrication_magnitude_is_reynolds_two_sphere_force(gap_frac):
+    # Two equal spheres of radius a approaching along their line of centres
+    # at relative speed V with a surface gap g << a: Reynolds lubrication
+    # between the two near-contact spheres gives the squeeze force
+    # 6 pi mu V a*^2 / g with the reduced radius a* = a a / (a + a) = a / 2
+    # (textbook asymptote, e.g. Kim & Karrila, Microhydrodynamics, Ch. 9).
+    # The paper's Eq. lubri with d = R_i + R_j (reading G22) is the same
+    # force, so a wrong prefactor, d = 2R as the diameter of one sphere of a
+    # different size, or d^2 in place of d, fails here.
+    a, mu, V = 1e-3, 2.5e-3, 0.013
+    g = gap_frac * a
+    c = _two_rigid_case([0.02, 0.02, 0.02], [0.02 + 2 * a + g, 0.02, 0.02], [V / 2, 0, 0],
+                        [-V / 2, 0, 0], R=a, eta=mu)
+    c["params"]["r_c"] = 3.9e-3
+    c["params"]["lub_gap_min"] = 0.01
+    s = oracle.OracleSim(c)
+    s.evaluate(1)
+    F = s.component("lub")
+    a_red = a * a / (a + a)
+    ref = 6 * math.pi * mu * V * a_red ** 2 / g
+    # the squeeze force pushes the approaching spheres apart
+    assert F[0][0] == pytest.approx(-ref, rel=1e-12)
+    assert F[1][0] == pytest.approx(ref, rel=1e-12)
+    assert F[0][1] == 0.0 and F[0][2] == 0.0
+
+
 def test_dem_coefficients_law1():
     p = cases.base_params()
     kn, kt, cn, ct = oracle.dem_coeffs(p, 1e-3, 1e-3, 2e-5, 2e-5)

@@ -104,6 +104,58 @@ def test_probe_reads_viscosity_of_exact_profile():
     assert mu_app == pytest.approx(mu, rel=2 * (dx / D) ** 2)
 
 
+@pytest.mark.parametrize("slip", [0.0, 0.37])
+def test_fit_reads_viscosity_of_exact_profile_whatever_the_slip(slip):
+    # Reading B6: a parabola fitted per half is exact on a field that carries
+    # the steady profile of Eq. poiseuanasol, with or without a slip
+    # velocity at the ends of the halves (where the mean-velocity read-out of
+    # Eq. poiseuave is biased), so the curvature gives mu to rounding.
+    c = cases.poiseuille_meso(nx=8, ny=48, nz=8, jitter=0.0)
+    p = c["params"]
+    mu, a, rho = p["eta"], p["body_amp"], p["rho0"]
+    D = 0.5 * p["box"][1]
+    y = c["x"][:, 1]
+    z = np.where(y < D, y, y - D)
+    prof = rho * a / (2 * mu) * (z * D - z * z) + slip
+    c["v"][:, 0] = np.where(y < D, prof, -prof)
+    s = oracle.OracleSim(c)
+    assert s.viscosity_fit(24) == pytest.approx(mu, rel=1e-9)
+    _, mu_app = s.profile(24)
+    if slip:
+        assert abs(mu_app / mu - 1) > 0.01
+
+
+def test_diagnostics_are_the_plain_sums():
+    # closed forms: a uniform drift U of every mobile particle has momentum
+    # M U, kinetic energy M U^2 / 2 and no kinetic temperature; adding
+    # +-w along x on alternate particles of equal mass gives temperature
+    # m w^2 / 3; a perfect lattice has number density 1/dx^3 everywhere
+    # (the kernel normalisation), walls excepted
+    c = cases.poiseuille_meso(nx=8, ny=8, nz=8, jitter=0.0)
+    n = len(c["x"])
+    U = np.array([0.3, -0.2, 0.1])
+    c["v"] = np.tile(U, (n, 1))
+    s = oracle.OracleSim(c)
+    s.neighbors()
+    s.density()
+    d = s.diagnostics()
+    M = c["mass"].sum()
+    assert np.allclose(d[0:3], M * U, rtol=1e-12)
+    assert d[3] == pytest.approx(0.5 * M * U @ U, rel=1e-12)
+    assert abs(d[4]) < 1e-12 * M * (U @ U)
+    assert d[5] == pytest.approx(np.linalg.norm(U), rel=1e-12)
+    dx = c["params"]["dx"]
+    assert d[6] == pytest.approx(1 / dx ** 3, rel=1e-12) and d[7] == pytest.approx(1 / dx ** 3, rel=1e-12)
+    assert d[8] == 0
+    w = 0.05
+    c["v"][:, 0] += np.where(np.arange(n) % 2 == 0, w, -w)
+    c["x"][3, 1] = np.nan
+    s2 = oracle.OracleSim(c)
+    d2 = s2.diagnostics()
+    assert d2[4] == pytest.approx(c["mass"][0] * w * w / 3, rel=1e-9)
+    assert d2[8] == 1
+
+
 def _transient_profile(y, t, a, nu, L, kmax=401):
     # start-up of the reverse-Poiseuille flow (square-wave forcing +a on
     # [0, L/2), -a on [L/2, L)): Fourier series of the diffusion equation.
