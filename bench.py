@@ -1,17 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the SDPD-DEM per-timestep interaction step on GB300.
 
-Workload: single-particle sedimentation, 32 x 32 x 64 fluid lattice
-(65,535 fluid + 1 DEM sphere, d = 4 dx, rho_s = 2500) with 4-layer
-dummy-particle walls in z (8,192 wall particles), dx = 1 mm, h = 3.9 dx,
-dt = 1e-5 s; synthetic seeded inputs.  A step is one full velocity-Verlet step
-(both sub-steps: neighbour build, density, drag, forces, integration,
-artificial viscosity).
+Default workload: the batched viscometer sweep, 64 reverse-Poiseuille slurry
+instances (fluid counts log-uniform in 20k-400k, solid fraction 0-30 % of
+DEM spheres of diameter 3 dx, temperature 280-350 K, forcing 1e-3-1e-1 m/s^2;
+about 9.46M particles) in one context, FP32 pair forces on FP64 state, one
+graph-captured launch sequence per step, autotuned; synthetic seeded inputs.
+A step is one full velocity-Verlet step (both sub-steps: neighbour build,
+density, drag, forces, integration) of every instance.
 
 Metric: SDPD-DEM pair updates/s = unordered pairs within h evaluated by the
 force pass x 2 evaluations per step x steps / time; also timesteps/s.  The
-headline runs the FP64 path; the split-precision path (FP32 pair arithmetic,
-FP64 state) is measured beside it on the same GPU.
+plain FP64 GPU path (double pair arithmetic, one context per instance, stage
+calls without a graph, default tuning) is timed beside it on the same GPU.
+Other workloads: --workload sedimentation | poiseuille | dambreak | surrogate.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -51,7 +53,8 @@ FLOPS_PER_PAIR = 160.0
 # particle: read x, v, w, F, N (5 x 24 B) and m, I (2 x 8 B), write x, v, w
 # (3 x 24 B)
 INTEGRATE_BYTES = 208.0
-# nominal ALU peaks from unit counts x maximum SM clock (152 SMs, 2070 MHz):
+# nominal ALU peaks from unit counts x maximum SM clock (152 SMs, 2070 MHz),
+# context only: the rooflines divide by the rates sdpd_alu_peaks measures;
 # FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM, 2 flops per FMA
 FP64_PEAK_TF = 152 * 2 * 2 * 2070e6 / 1e12
 FP32_PEAK_TF = 152 * 128 * 2 * 2070e6 / 1e12
@@ -63,15 +66,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "split"],
+                    help="pair arithmetic of the timed path (auto: the workload's own, "
+                         "split for the batch and the dam break, fp64 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sedimentation", choices=sorted(WORKLOADS))
     ap.add_argument("--paths", default="both", choices=["both", "main"],
-                    help="also time the other precision path (both) or not")
+                    help="also time the comparison path (both) or not")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 comparison path (per instance)")
     ap.add_argument("--max-neighbors", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (force variant, skin, block size) and use the defaults")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.precision == "auto":
+        a.precision = "split" if a.workload in ("batch", "dambreak") else "fp64"
+    return a
 
 
 def dist_env():
@@ -142,9 +152,129 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ native
-def time_native(args, ws, rank, local):
+def _timed(stream, fn, flush=None):
+    """Milliseconds of fn() on `stream` by CUDA events, L2 flushed before."""
+    import torch
+    if flush is not None:
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def time_graph_path(case, precision, args, local, stream, flush, ws):
+    """The product path: one context holding every instance of the workload,
+    autotuned, whole steps replayed from the captured CUDA graph.  Also times
+    the dominant kernel (force pass), the density pass and the update alone,
+    and the end-to-end step through the C ABI with host buffers."""
     import torch
     import torch.distributed as dist
+
+    from paper_2002_03120_gb300 import binding as B
+    setting = None
+    if not args.no_tune:
+        from paper_2002_03120_gb300 import autotune
+        setting = autotune.tune(case, precision=precision, max_neighbors=args.max_neighbors)
+    sim = B.Sim(case, precision=precision, max_neighbors=args.max_neighbors)
+    if setting:
+        from paper_2002_03120_gb300 import autotune
+        autotune.apply(sim, setting)
+    sim.build_cells(stream)
+    torch.cuda.synchronize()
+    pairs = sim.count_pairs()
+    with torch.cuda.stream(stream):
+        sim.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            ms.append(_timed(stream, lambda: sim.step(1, stream), flush))
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    kernels = sim.graph_kernels()
+    # dominant kernel (force pass, velver 1) timed alone on the stream it is
+    # launched on, L2 flushed before each launch
+    fms = []
+    for _ in range(5):
+        sim.evaluate(1, stream)  # build, density, drag for the current state
+        fms.append(_timed(stream, lambda: sim.compute_forces(1, stream), flush))
+    # the density pass (density, EOS, and the filter or reinitialisation
+    # where the workload has them) timed alone after a list build
+    dms = []
+    for _ in range(5):
+        sim.build_cells(stream)
+        dms.append(_timed(stream, lambda: sim.compute_density(stream), flush))
+    sim.couple_drag(stream)   # leave the stage sequence complete
+    torch.cuda.synchronize()
+    # the HBM-bound update kernel alone (velocity Verlet, velver 1)
+    ims = [_timed(stream, lambda: sim.integrate(1, stream), flush) for _ in range(5)]
+    # end-to-end through the C ABI with host buffers: upload the step's state
+    # from pinned memory, run the step, read the result back
+    N = sim.N
+    hx = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
+    hv = torch.empty_like(hx)
+    hw = torch.empty_like(hx)
+    sim.download_state(hx, hv, hw, stream=stream)
+    torch.cuda.synchronize()
+
+    def e2e_step():
+        sim.upload_state(hx, hv, hw, stream=stream)
+        sim.step(1, stream)
+        sim.download_state(hx, hv, hw, stream=stream)
+    e2e_ms = [_timed(stream, e2e_step, flush) for _ in range(max(3, args.steps // 2))]
+    mobile = int(sum(int(np.sum(c["type"] <= 1)) for c in sim.cases))
+    out = dict(pairs=pairs, ms=float(sum(ms)), per_step=ms, kernels=kernels,
+               force_ms=float(np.median(fms)), density_ms=float(np.median(dms)),
+               e2e_ms=float(np.mean(e2e_ms)), integrate_ms=float(np.median(ims)), mobile=mobile,
+               setting=setting, e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N,
+               instances=len(sim.cases))
+    sim.close()
+    return out
+
+
+def time_plain_fp64(case, args, stream, flush):
+    """The plain FP64 GPU path the metric compares with: the same kernels with
+    double pair arithmetic, each instance in a context of its own, the stages
+    launched one by one (no CUDA graph), default tuning.  Returns the summed
+    per-step time over the instances and the pairs evaluated per step."""
+    import torch
+
+    from paper_2002_03120_gb300 import binding as B
+    insts = case if isinstance(case, list) else [case]
+    steps = max(1, args.fp64_steps)
+    tot_ms = 0.0
+    pairs = 0
+    for c in insts:
+        sim = B.Sim(c, precision=B.SDPD_PREC_FP64, max_neighbors=args.max_neighbors)
+
+        def one_step():
+            for velver in (1, 2):
+                sim.build_cells(stream)
+                sim.compute_density(stream)
+                sim.couple_drag(stream)
+                sim.compute_forces(velver, stream)
+                sim.integrate(velver, stream)
+        sim.build_cells(stream)
+        torch.cuda.synchronize()
+        pairs += sim.count_pairs()
+        one_step()   # warm-up
+        tot_ms += sum(_timed(stream, one_step, flush) for _ in range(steps)) / steps
+        sim.check()
+        sim.close()
+    return dict(ms_per_step=tot_ms, pairs=pairs, steps=steps, instances=len(insts))
+
+
+def time_native(args, ws, rank, local):
+    import torch
 
     from paper_2002_03120_gb300 import binding as B
 
@@ -153,120 +283,16 @@ def time_native(args, ws, rank, local):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     case = make_case(args.workload)
+    peaks = B.alu_peaks()   # this GPU's FP32 / FP64 / INT32 rates at its current clock
     prec = B.SDPD_PREC_FP64 if args.precision == "fp64" else B.SDPD_PREC_SPLIT
-
-    def run_path(precision):
-        setting = None
-        if not args.no_tune:
-            from paper_2002_03120_gb300 import autotune
-            setting = autotune.tune(case, precision=precision, max_neighbors=args.max_neighbors)
-        sim = B.Sim(case, precision=precision, max_neighbors=args.max_neighbors)
-        if setting:
-            autotune.apply(sim, setting)
-        sim.build_cells(stream)
-        torch.cuda.synchronize()
-        pairs = sim.count_pairs()
-        with torch.cuda.stream(stream):
-            sim.step(args.warmup, stream)
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        ms = []
-        with ClockSampler(local) as clk:
-            for _ in range(args.steps):
-                with torch.cuda.stream(stream):
-                    flush.fill_(1.0)
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                sim.step(1, stream)
-                e1.record(stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        total_ms = float(sum(ms))
-        kernels = sim.graph_kernels()
-        # dominant kernel (force pass, velver 1) timed alone on the stream it
-        # is launched on, L2 flushed before each launch
-        fms = []
-        for _ in range(5):
-            sim.evaluate(1, stream)  # build, density, drag for the current state
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sim.compute_forces(1, stream)
-            b.record(stream)
-            b.synchronize()
-            fms.append(a.elapsed_time(b))
-        # the density pass (density, EOS, and the filter or reinitialisation
-        # where the workload has them) timed alone after a list build
-        dms = []
-        for _ in range(5):
-            sim.build_cells(stream)
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sim.compute_density(stream)
-            b.record(stream)
-            b.synchronize()
-            dms.append(a.elapsed_time(b))
-        sim.couple_drag(stream)   # leave the stage sequence complete
-        torch.cuda.synchronize()
-        # the HBM-bound update kernel alone (velocity Verlet, velver 1: kick
-        # and drift; the velver-2 call also runs the collision pass)
-        ims = []
-        for _ in range(5):
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sim.integrate(1, stream)
-            b.record(stream)
-            b.synchronize()
-            ims.append(a.elapsed_time(b))
-        # end-to-end through the C ABI with host buffers: upload the step's
-        # state from pinned memory, run the step, read the result back
-        N = sim.N
-        hx = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
-        hv = torch.empty_like(hx)
-        hw = torch.empty_like(hx)
-        sim.download_state(hx, hv, hw, stream=stream)
-        torch.cuda.synchronize()
-        e2e_ms = []
-        for _ in range(max(3, args.steps // 2)):
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sim.upload_state(hx, hv, hw, stream=stream)
-            sim.step(1, stream)
-            sim.download_state(hx, hv, hw, stream=stream)
-            b.record(stream)
-            b.synchronize()
-            e2e_ms.append(a.elapsed_time(b))
-        mobile = int(sum(int(np.sum(c["type"] <= 1)) for c in sim.cases))
-        out = dict(pairs=pairs, ms=total_ms, per_step=ms, kernels=kernels,
-                   force_ms=float(np.median(fms)), density_ms=float(np.median(dms)),
-                   e2e_ms=float(np.mean(e2e_ms)),
-                   integrate_ms=float(np.median(ims)), mobile=mobile, setting=setting,
-                   e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N)
-        sim.close()
-        return out
-
-    main = run_path(prec)
+    main = time_graph_path(case, prec, args, local, stream, flush, ws)
     other = None
     if args.paths == "both":
-        other = run_path(B.SDPD_PREC_SPLIT if prec == B.SDPD_PREC_FP64 else B.SDPD_PREC_FP64)
-    return main, other
+        if prec == B.SDPD_PREC_SPLIT:
+            other = time_plain_fp64(case, args, stream, flush)
+        else:
+            other = time_graph_path(case, B.SDPD_PREC_SPLIT, args, local, stream, flush, 1)
+    return main, other, peaks
 
 
 def time_surrogate(args, ws, rank, local):
@@ -378,26 +404,69 @@ def max_over_ranks(v, ws):
     return float(t.item())
 
 
-def cpu_baseline(seconds=15.0):
-    """The FP64 oracle timed on this host's cores on a bounded sample of the
-    workload: full steps of a 16x16x32 sedimentation box (1/8 of the lattice,
-    same physics), until `seconds` of CPU time have elapsed."""
-    import oracle
+def oracle_sample(workload, case=None):
+    """A bounded sample of the workload the oracle can step in seconds: the
+    smallest instance of the batch (full size), or a smaller box of the
+    single-instance workloads with the same physics."""
     from paper_2002_03120_gb300 import cases
-    case = cases.sedimentation(nx=16, ny=16, nz=32)
-    sim = oracle.OracleSim(case)
-    sim.neighbors()
-    pairs = _oracle_pairs(sim, case)
-    t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < seconds:
-        sim.run(1)
-        steps += 1
-    dt = time.perf_counter() - t0
-    return dict(value=pairs * 2 * steps / dt, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{steps} full steps of sedimentation 16x16x32 ({len(case['x'])} particles, "
-                       f"{pairs} pairs/evaluation), FP64, single thread",
-                steps_per_s=steps / dt)
+    if workload == "batch":
+        insts = case if case is not None else cases.viscometer_batch()
+        sizes = [len(c["x"]) for c in insts]
+        k = int(np.argmin(sizes))
+        return insts[k], k, f"instance {k} of the 64-instance batch ({sizes[k]} particles, full size)"
+    if workload == "dambreak":
+        c = cases.dam_break(scale=0.25, n_spheres=156)
+        return c, 0, f"dam break at 1/4 linear scale ({len(c['x'])} particles, 156 spheres)"
+    if workload == "poiseuille":
+        c = cases.poiseuille_si()
+        return c, 0, f"reverse Poiseuille 16x32x16 ({len(c['x'])} particles, full size)"
+    c = cases.sedimentation(nx=16, ny=16, nz=32)
+    return c, 0, f"sedimentation 16x16x32 ({len(c['x'])} particles, 1/8 of the lattice)"
+
+
+def cpu_baseline(workload, seconds=12.0, case=None):
+    """The FP64 oracle, as it stands, timed on this host's cores on a bounded
+    sample of the workload: full steps of oracle_sample() until `seconds`
+    have elapsed, once on one thread and once on every core (OpenMP over
+    particles; the same results)."""
+    import oracle
+    case, inst, what = oracle_sample(workload, case)
+    nproc = os.cpu_count() or 1
+    runs = {}
+    for nt in (1, nproc):
+        used = oracle.threads(nt)
+        sim = oracle.OracleSim(case, inst=inst)
+        sim.neighbors()
+        pairs = _oracle_pairs(sim, case)
+        sim.run(1)   # warm-up step
+        t0 = time.perf_counter()
+        steps = 0
+        while time.perf_counter() - t0 < seconds or steps == 0:
+            sim.run(1)
+            steps += 1
+        dt = time.perf_counter() - t0
+        runs[nt] = dict(value=pairs * 2 * steps / dt, steps=steps, seconds=dt, threads=used,
+                        steps_per_s=steps / dt, pairs=pairs)
+    allc = runs[nproc]
+    one = runs[1]
+    return dict(value=allc["value"], unit=UNIT, cores=allc["threads"], kind="oracle",
+                sample=f"{allc['steps']} full steps of {what}, {allc['pairs']} pairs/evaluation, FP64, "
+                       f"{allc['threads']} threads (all host cores)",
+                steps_per_s=allc["steps_per_s"], host_cores=nproc, host_cpu=_cpu_name(),
+                single_thread={"value": one["value"], "unit": UNIT, "cores": 1,
+                               "sample": f"{one['steps']} full steps of the same sample, 1 thread",
+                               "steps_per_s": one["steps_per_s"]})
+
+
+def _cpu_name():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def _oracle_pairs(sim, case):
@@ -446,6 +515,34 @@ def measured_peaks():
         return {}
 
 
+def reference_arm(args):
+    """bench.py --impl reference: the oracle, as it stands, on every host core,
+    each step one full step of the bounded sample of the workload."""
+    import oracle
+    case, inst, what = oracle_sample(args.workload)
+    cores = oracle.threads(os.cpu_count() or 1)
+    sim = oracle.OracleSim(case, inst=inst)
+    sim.neighbors()
+    pairs = _oracle_pairs(sim, case)
+    for _ in range(args.warmup):
+        sim.run(1)
+    ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sim.run(1)
+        ms.append((time.perf_counter() - t0) * 1e3)
+    tot = sum(ms) / 1e3
+    val = pairs * 2 * args.steps / tot
+    sample = f"{what} per step; FP64 oracle on {cores} threads (all host cores)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -453,78 +550,49 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if args.impl == "native" else "gloo")
     if args.impl == "reference":
-        if rank != 0:
-            return
-        ms = []
-        import oracle
-        from paper_2002_03120_gb300 import cases
-        case = cases.sedimentation(nx=16, ny=16, nz=32)
-        sim = oracle.OracleSim(case)
-        sim.neighbors()
-        pairs = _oracle_pairs(sim, case)
-        for _ in range(args.warmup):
-            sim.run(1)
-        for _ in range(args.steps):
-            t0 = time.perf_counter()
-            sim.run(1)
-            ms.append((time.perf_counter() - t0) * 1e3)
-        tot = sum(ms) / 1e3
-        val = pairs * 2 * args.steps / tot
-        sample = (f"sedimentation 16x16x32 ({len(case['x'])} particles) per step, the 32x32x64 "
-                  f"workload's physics at 1/8 of its lattice; FP64 oracle, single thread")
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS["sedimentation"], "sample": sample},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        if rank == 0:
+            reference_arm(args)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
-
     if args.workload == "surrogate":
         time_surrogate(args, ws, rank, local)
         if ws > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    main_r, other_r = time_native(args, ws, rank, local)
+    main_r, other_r, alu = time_native(args, ws, rank, local)
     t_max = max_over_ranks(main_r["ms"], ws)
     pairs = main_r["pairs"]
     value = pairs * 2 * args.steps * ws / (t_max / 1e3)
-    steps_per_s = args.steps / (t_max / 1e3)
-    other_val = other_r["pairs"] * 2 * args.steps / (other_r["ms"] / 1e3) if other_r else None
+    split = args.precision == "split"
     peaks = measured_peaks()
-    # ncu counters of the profiled kernels of this workload (the dam break's
-    # were taken at half scale, DRAM bytes scaled by the particle ratio)
-    cnt = ncu_counters({"sedimentation": "counters_sedimentation",
-                        "dambreak": "counters_dambreak"}.get(args.workload, "none"))
-    fp64 = args.precision == "fp64"
-    integ_cnt = ncu_counters("counters_integrate").get(f"k_integrate<{'double' if fp64 else 'float'}>", {})
-    # dominant kernel: the force pass (k_force_half + k_force_gather + the
-    # sphere kernel), ALU bound; algorithmic flops = 160 per unordered pair
-    force_flops = FLOPS_PER_PAIR * pairs
-    achieved_tf = force_flops / (main_r["force_ms"] / 1e3) / 1e12
-    other_tf = FLOPS_PER_PAIR * other_r["pairs"] / (other_r["force_ms"] / 1e3) / 1e12 if other_r else None
-    def force_kernel(res, double):
-        # the phase-1 kernel of the Newton-3 pass, or the direct pass
-        n3 = (res or {}).get("setting") or {}
-        name = "k_force_half" if n3.get("newton3", 1) else "k_force_fluid"
-        return f"{name}<{'double' if double else 'float'}>"
-    main_k = force_kernel(main_r, fp64)
-    other_k = force_kernel(other_r, not fp64)
-    fp64_peak_tf = FP64_PEAK_TF if fp64 else FP32_PEAK_TF
+    # ncu counters of the profiled kernels of this workload (captured on a
+    # reduced case, DRAM bytes scaled by the particle ratio; see profiles/)
+    cnt = ncu_counters({"sedimentation": "counters_sedimentation", "dambreak": "counters_dambreak",
+                        "batch": "counters_batch"}.get(args.workload, "none"))
+    integ_cnt = ncu_counters("counters_integrate").get(f"k_integrate<{'float' if split else 'double'}>", {})
+    n3 = (main_r.get("setting") or {}).get("newton3", 1)
+    main_k = f"{'k_force_half' if n3 else 'k_force_fluid'}<{'float' if split else 'double'}>"
+    # the force pass is bound by arithmetic issue: algorithmic flops = 160 per
+    # unordered pair, against this GPU's measured FMA rate of the path's
+    # precision (sdpd_alu_peaks, run at the start of this bench)
+    peak_tf = alu["fp32_tflops"] if split else alu["fp64_tflops"]
+    achieved_tf = FLOPS_PER_PAIR * pairs / (main_r["force_ms"] / 1e3) / 1e12
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32 pairs / f64 state",
+        "dtype": "f32 pairs / f64 state" if split else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "particles": main_r["N"], "pairs_per_eval": pairs,
-                   "evals_per_step": 2, "precision": args.precision,
-                   "l2": "flushed (256 MB write) before every timed step",
+        "config": {"workload": WORKLOADS[args.workload], "instances": main_r["instances"],
+                   "particles": main_r["N"], "pairs_per_eval": pairs, "evals_per_step": 2,
+                   "precision": args.precision,
+                   "l2": "inputs larger than L2, and L2 flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{ws}",
                    "tuning": main_r["setting"] or "defaults (newton3 1, skin 0.03, block 128)"},
-        "timesteps_per_s": steps_per_s,
+        "timesteps_per_s": args.steps / (t_max / 1e3),
         "density_pass": {"ms_per_launch": main_r["density_ms"], "pairs": pairs,
                          "pair_evals_per_s": pairs / (main_r["density_ms"] / 1e3),
                          "note": "density + EOS (+ filter or reinitialisation where the workload "
@@ -533,18 +601,19 @@ def main():
                     "max": float(np.max(main_r["per_step"]))},
         "gpu_launches": main_r["kernels"] * args.steps,
         "clocks": main_r["clocks"],
-        "roofline": {"kernel": ("force pass (k_force_half + k_force_gather + k_force_rigid), velver 1"
-                                if main_k.startswith("k_force_half") else
-                                "force pass (k_force_fluid + k_force_rigid), velver 1"),
-                     "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp64_peak_tf,
+        "roofline": {"kernel": f"force pass ({main_k} with the sphere kernel), velver 1",
+                     "bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / peak_tf,
                      "traffic": cnt.get(main_k, {}).get("dram_bytes_per_launch"),
                      "ms_per_launch": main_r["force_ms"],
-                     "pipe_util_ncu": pipe_util(cnt.get(main_k), fp64),
-                     "note": ("peak = %s nominal from unit counts x max clock (2070 MHz); "
-                              "achieved counts 160 flop per unordered pair (both directions of the "
-                              "direct pass count once); traffic = ncu DRAM bytes of %s per launch "
-                              "(profiles/)") % ("FP64" if fp64 else "FP32", main_k)},
+                     "pipe_util_ncu": pipe_util(cnt.get(main_k), not split),
+                     "note": ("peak = this GPU's %s FMA rate measured by sdpd_alu_peaks at the start of "
+                              "this run (register-resident FMA chains, CUDA events); achieved counts 160 "
+                              "flop per unordered pair (both directions of the direct pass count once); "
+                              "the Philox integer work is on top (see alu_peaks.int32_tops); traffic = ncu "
+                              "DRAM bytes of %s per launch (profiles/)") % ("FP32" if split else "FP64", main_k)},
+        "alu_peaks": {**alu, "nominal_fp32_tflops": FP32_PEAK_TF, "nominal_fp64_tflops": FP64_PEAK_TF,
+                      "note": "measured at the clock of this run; nominal = unit counts x 2070 MHz"},
         "hbm_kernel": {"kernel": "k_integrate (velver 1: kick + drift)", "bound": "hbm",
                        "achieved": main_r["mobile"] * INTEGRATE_BYTES / (main_r["integrate_ms"] / 1e3) / 1e9,
                        "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
@@ -553,27 +622,32 @@ def main():
                        "bytes_per_particle": INTEGRATE_BYTES, "particles": main_r["mobile"],
                        "ms_per_launch": main_r["integrate_ms"],
                        "fp64_pipe_ncu": integ_cnt.get("fp64_pipe_pct", 100.0) / 100.0 if integ_cnt else None,
-                       "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json); the kernel also "
-                               "keeps the cell-relative mirrors current (xl64, dsp, A32, A64: about 190 B "
-                               "more per particle), which the algorithmic bytes do not count.  Its bound "
-                               "is the FP64 pipe, not HBM: the kicks (with the exactly rounded division), "
-                               "the drift and the mirror updates are FP64 (fp64_pipe_ncu: busy fraction "
-                               "from profiles/counters_integrate.json)"},
+                       "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json); algorithmic bytes: "
+                               "read x, v, w, F, N, m, I and write x, v, w of each mobile particle"},
         "e2e": {"value": pairs * 2 / (main_r["e2e_ms"] / 1e3) * ws, "unit": UNIT,
                 "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
-        "split_precision" if fp64 else "fp64_path": None if other_r is None else {
-            "value": other_val, "unit": UNIT, "ms_per_step": other_r["ms"] / args.steps,
-            "force_ms_per_launch": other_r["force_ms"], "tuning": other_r["setting"],
-            "speedup_vs_fp64": (other_val / (value / ws)) if fp64 else None,
-            "roofline": {"bound": "alu", "achieved": other_tf,
-                         "peak": FP32_PEAK_TF if fp64 else FP64_PEAK_TF, "unit": "TFLOP/s",
-                         "frac": other_tf / (FP32_PEAK_TF if fp64 else FP64_PEAK_TF),
-                         "traffic": cnt.get(other_k, {}).get("dram_bytes_per_launch"),
-                         "pipe_util_ncu": pipe_util(cnt.get(other_k), not fp64)}},
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "sedimentation":
-        rec["cpu_baseline"] = cpu_baseline()
+    if other_r is not None and split:
+        fp64_val = other_r["pairs"] * 2 / (other_r["ms_per_step"] / 1e3)
+        rec["fp64_path"] = {
+            "value": fp64_val, "unit": UNIT, "ms_per_step": other_r["ms_per_step"],
+            "timesteps_per_s": 1e3 / other_r["ms_per_step"], "steps_timed": other_r["steps"],
+            "speedup_of_value": (value / ws) / fp64_val,
+            "note": "plain FP64 GPU path: double pair arithmetic, each of the %d instances in its own "
+                    "context, stage calls without a graph, default tuning; per-step time summed over "
+                    "the instances" % other_r["instances"]}
+    elif other_r is not None:
+        other_val = other_r["pairs"] * 2 * args.steps / (other_r["ms"] / 1e3)
+        otf = FLOPS_PER_PAIR * other_r["pairs"] / (other_r["force_ms"] / 1e3) / 1e12
+        rec["split_precision"] = {
+            "value": other_val, "unit": UNIT, "ms_per_step": other_r["ms"] / args.steps,
+            "force_ms_per_launch": other_r["force_ms"], "tuning": other_r["setting"],
+            "speedup_vs_fp64": other_val / (value / ws),
+            "roofline": {"bound": "alu", "achieved": otf, "peak": alu["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": otf / alu["fp32_tflops"]}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline(args.workload, case=None)
     if rank == 0:
         print(json.dumps(rec))
     if ws > 1:
