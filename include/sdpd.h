@@ -217,7 +217,14 @@ sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
  * (one of the two particles owns it, chosen by a hash of the pair so that
  * each owns about half of its list; its result goes to the partner through a
  * pair buffer; deterministic, no atomics); newton3 = 0 evaluates every pair
- * from both sides.  Both give the same forces up to summation order.
+ * from both sides, one thread per particle walking its list; newton3 = 2 is
+ * the same pass as 0 with the pairs streamed through shared memory: a warp
+ * compacts the pairs within h of its 32 particles' lists and evaluates them
+ * 32 at a time, each particle summing its own in list order (forces equal to
+ * those of 0 bit for bit); newton3 = 3 is that pass with its registers
+ * capped for three 256-thread blocks per SM instead of two (a tuning choice;
+ * FP32 pairs only, FP64 runs 2).  All give the same forces up to summation
+ * order.
  * Invalidates the current neighbour build and graph.  Synchronous. */
 sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
 

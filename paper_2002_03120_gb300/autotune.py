@@ -1,8 +1,9 @@
 """Autotuner of the per-workload launch choices of libsdpd.
 
 For one workload (a list of instances and a precision) it times full steps
-under each candidate setting -- force-pass variant (Newton-3 half pairs or
-direct), Verlet skin, pair-kernel block size -- picks the fastest, and keeps
+under each candidate setting -- force-pass variant (Newton-3 half pairs,
+direct, or the pair stream through shared memory at two register caps),
+Verlet skin, pair-kernel block size -- picks the fastest, and keeps
 the choice in a JSON file keyed by GPU name, precision and size class (total
 particles rounded to a power of two, number of instances), so later contexts
 of the same class reuse it without measuring again.
@@ -21,8 +22,10 @@ import os
 from . import binding as B
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sdpd_gb300", "autotune.json")
+# force-pass variants (sdpd_set_force_mode): 1 Newton 3, 0 direct, 2 pair
+# stream (two 256-thread blocks per SM), 3 pair stream (three, FP32 only)
 CANDIDATES = {
-    "newton3": (1, 0),
+    "newton3": (1, 0, 2, 3),
     "skin": (0.0, 0.03, 0.06, 0.12),
     "block": (64, 128, 256),
 }
@@ -56,8 +59,24 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
     os.replace(tmp, path)
 
 
-def search(measure, candidates=CANDIDATES):
-    """Exhaustive search over the candidate grid; `measure(setting)` returns a
+def _sampled(setting, candidates, precision):
+    """Settings measured: the Newton-3 pass over the whole grid; the direct
+    pass at the default block (every skin) and without skin (every block);
+    the pair stream at the two larger blocks and the two middle skins, the
+    three-block variant for FP32 pairs only."""
+    mode, skin, block = setting["newton3"], setting["skin"], setting["block"]
+    skins = candidates["skin"]
+    if mode == 0:
+        return skin == skins[0] or block == 128
+    if mode in (2, 3):
+        if mode == 3 and precision == B.SDPD_PREC_FP64:
+            return False
+        return block in (128, 256) and skin in skins[1:3]
+    return True
+
+
+def search(measure, candidates=CANDIDATES, precision=None):
+    """Search over the sampled candidate grid; `measure(setting)` returns a
     time in ms (or None when the setting is not usable).  Returns
     (best_setting, table of all results)."""
     keys = sorted(candidates)
@@ -65,9 +84,8 @@ def search(measure, candidates=CANDIDATES):
     best, best_t = None, float("inf")
     for values in itertools.product(*(candidates[k] for k in keys)):
         setting = dict(zip(keys, values))
-        if setting["newton3"] == 0 and setting["skin"] != candidates["skin"][0] and \
-                setting["block"] != 128:
-            continue  # the direct pass is sampled at the default block only
+        if not _sampled(setting, candidates, precision):
+            continue
         t = measure(setting)
         table.append({**setting, "ms": t})
         if t is not None and t < best_t:
@@ -93,11 +111,15 @@ def tune(cases, precision=B.SDPD_PREC_SPLIT, steps=10, warmup=3, cache_path=DEFA
     if not force and key in cache:
         return cache[key]["best"]
     stream = torch.cuda.Stream()
+    # one context for every setting: the starting state is restored from a
+    # checkpoint image before each measurement (no re-upload of the particles)
+    sim = B.Sim(cases, precision=precision, max_neighbors=max_neighbors)
+    image = sim.checkpoint()
 
     def measure(setting):
-        sim = B.Sim(cases, precision=precision, max_neighbors=max_neighbors)
         try:
             apply(sim, setting)
+            sim.restore(image)
             sim.step(warmup, stream)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -108,10 +130,11 @@ def tune(cases, precision=B.SDPD_PREC_SPLIT, steps=10, warmup=3, cache_path=DEFA
             return a.elapsed_time(b) / steps
         except B.SdpdError:
             return None
-        finally:
-            sim.close()
 
-    best, table = search(measure, candidates)
+    try:
+        best, table = search(measure, candidates, precision)
+    finally:
+        sim.close()
     cache[key] = {"best": best, "table": table, "particles": n, "instances": len(cases)}
     save_cache(cache, cache_path)
     return best

@@ -53,7 +53,7 @@ struct sdpd_ctx {
     Inst *d_inst = nullptr;
     int any_filter = 0, any_artvis = 0, any_reinit = 0;
     std::vector<double> probe_y;   // mean slab positions of the last viscosity probe
-    int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct
+    int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct, 2/3 pair stream
     int noise_cache = 1;               // second evaluation of a step reuses the first one's normals
     double skin = 0.03;                // Verlet skin as a fraction of h
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
@@ -385,7 +385,7 @@ sdpd_status ensure_geometry(sdpd_ctx *c)
 void enqueue_build(sdpd_ctx *c, cudaStream_t st, const int *gate = nullptr)
 {
     c->b.use_cache = c->noise_cache;
-    launch_build(c->b, c->precision, c->newton3, gate, st);
+    launch_build(c->b, c->precision, c->newton3 == 1, gate, st);
 }
 
 }  // namespace
@@ -413,6 +413,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(SDPD_E_CUDA, "no CUDA device");
+    init_pair_kernels();   // kernel attributes, set outside any stream capture
     sdpd_ctx *c = new sdpd_ctx();
     c->n_inst = n_instances;
     c->precision = precision;
@@ -774,7 +775,7 @@ sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
     (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->cells_valid) return fail(SDPD_E_STATE, "sdpd_build_cells must precede sdpd_compute_density");
-    launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, nullptr, (cudaStream_t)stream);
+    launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, nullptr, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     c->density_valid = true;
     return SDPD_OK;
@@ -834,7 +835,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         c->density_valid = false;
     }
     if (!c->density_valid) {
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, nullptr, st);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, nullptr, st);
         c->density_valid = true;
     }
     if (!c->graph) {
@@ -848,12 +849,12 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         // at velver 1 only after such a build, at velver 2 always
         cudaStream_t cs = c->cap_stream;
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, c->b.fresh, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, c->b.fresh, cs);
         launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 1, c->newton3, cs);
         launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3, nullptr, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, nullptr, cs);
         launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 2, c->newton3, cs);
         launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);
@@ -874,7 +875,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
 sdpd_status sdpd_set_force_mode(sdpd_ctx *c, int newton3)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
-    if (newton3 != 0 && newton3 != 1) return fail(SDPD_E_INVALID, "newton3 must be 0 or 1");
+    if (newton3 < 0 || newton3 > 3) return fail(SDPD_E_INVALID, "force mode must be 0, 1, 2 or 3");
     CUDA_TRY(cudaDeviceSynchronize());
     if (newton3 != c->newton3) {
         c->newton3 = newton3;

@@ -363,7 +363,9 @@ void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, c
 // reinitialises the density
 void launch_density(const Bufs &b, int precision, int dflags, int newton3, const int *gate, cudaStream_t st);
 void launch_drag(const Bufs &b, int precision, cudaStream_t st);
+// force mode: 0 direct, 1 Newton 3 (half pairs + gather), 2 pair stream
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st);
+void init_pair_kernels();
 void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st);
 void launch_integrate(const Bufs &b, int precision, int velver, int any_artvis, cudaStream_t st);
 void launch_step_done(const Bufs &b, cudaStream_t st);

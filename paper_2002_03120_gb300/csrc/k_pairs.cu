@@ -655,6 +655,16 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// Kernel weight W(r) = Wc (1 + 3q)(1 - q)^3 of a pair for the drag reaction
+// (Eq. F_fpi_DG_reac), every rounding explicit.
+template <class R>
+__device__ __forceinline__ R drag_weight(const PairK<R> &P, R q, R om)
+{
+    return mul_rn(mul_rn(mul_rn(mul_rn(P.Wc, fma_rn(R(3), q, R(1))), om), om), om);
+}
 
 template <class R> struct Z6 {
     R z0, z1, z2, z3, z4, z5;
@@ -886,21 +896,25 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
             zA[at] = zw;
             zB[at] = zv;
         }
+        // every accumulation step rounded explicitly (the pair-stream pass
+        // adds the same terms in the same order and must match bit for bit)
+        R gx, gy, gz, hx, hy, hz;
+        pair_fh(ox, oy, oz, ce, ex, ey, ez, gx, gy, gz, hx, hy, hz);
         if (rig) {
             // Eq. F_fpi_DG_reac: -F^DG_s W_sj / S_s
             R rcx, rcy, rcz;
             rxn_of(b, j, rcx, rcy, rcz);
-            const R W = P.Wc * (R(1) + R(3) * q) * om * om * om;
-            fx -= rcx * W;
-            fy -= rcy * W;
-            fz -= rcz * W;
+            const R W = drag_weight(P, q, om);
+            fx = sub_rn(fx, mul_rn(rcx, W));
+            fy = sub_rn(fy, mul_rn(rcy, W));
+            fz = sub_rn(fz, mul_rn(rcz, W));
         }
-        fx += ox + ce * ex;
-        fy += oy + ce * ey;
-        fz += oz + ce * ez;
-        tx += ey * oz - ez * oy;
-        ty += ez * ox - ex * oz;
-        tz += ex * oy - ey * ox;
+        fx = add_rn(fx, gx);
+        fy = add_rn(fy, gy);
+        fz = add_rn(fz, gz);
+        tx = add_rn(tx, hx);
+        ty = add_rn(ty, hy);
+        tz = add_rn(tz, hz);
     }
     write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, P.lev);
 }
@@ -925,6 +939,219 @@ __global__ void __launch_bounds__(256) k_force_fluid(Bufs b, int velver)
     } else {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
             force_fluid_slot<R, false>(b, base + (threadIdx.x & 31), step, fill);
+    }
+}
+
+// ---------------------------------------------------- pair-stream force pass
+// The direct pass (every pair from both sides) reorganised for the SIMT
+// lanes: a warp owns 32 consecutive slots; phase A walks the 32 lists in
+// step (the exact r < h decision, cheap) and compacts the surviving pairs
+// into a ring in shared memory with ballots; phase B evaluates them 32 at a
+// time -- Philox, Box-Muller and the SDPD pair of Eqs. FijC-FijT, or the
+// fluid-sphere pair with the drag reaction -- with every lane busy whatever
+// the spread of list lengths and of pairs beyond h; phase C hands each
+// result back to the lane that owns the particle, which adds its pairs in
+// list order.  The particle's own records are staged in shared memory for
+// phase B.  The terms and their order are those of force_fluid_slot, so the
+// forces equal the direct pass bit for bit.
+template <class R> struct StreamSmem {
+    using T4 = typename Vec<R>::T4;
+    T4 qr[64];            // queued pairs: r_ij (x, y, z) and r^2
+    T4 hB[32], hC[32], hD[32];   // records of the warp's own particles
+    int2 qm[64];          // partner slot; entry k << 8 | owner lane << 1 | sphere partner
+    int hinst[32];        // instance of each own particle
+    R res[32 * 9];        // per batch position: f part (3), e x o (3), drag reaction (3)
+};
+
+template <class R, bool REUSE>
+__device__ __forceinline__ void force_stream_group(const Bufs &b, StreamSmem<R> &S, long long base, uint32_t step,
+                                                   bool fill)
+{
+    using T4 = typename Vec<R>::T4;
+    using T2 = typename Vec2<R>::T2;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const long long s = base + lane;
+    const long long Np = b.Npad;
+    const T4 *__restrict__ A = Mir<R>::A(b);
+    const T4 *__restrict__ Bm = Mir<R>::B(b);
+    const T4 *__restrict__ Cm = Mir<R>::C(b);
+    const T4 *__restrict__ Dm = Mir<R>::D(b);
+    T4 *__restrict__ zA = (T4 *)b.zdA;
+    T2 *__restrict__ zB = (T2 *)b.zdB;
+    const bool mine = s < b.N && b.stype[s] == T_FLUID;
+    int gi = 0, ii = 0, n = 0;
+    T4 Ai;
+    if (mine) {
+        gi = b.perm[s];
+        ii = b.pinst[gi];
+        n = b.ncnt[s];
+        Ai = A[s];
+        S.hB[lane] = Bm[s];
+        S.hC[lane] = Cm[s];
+        S.hD[lane] = Dm[s];
+    }
+    S.hinst[lane] = ii;
+    const Inst &I = b.inst[ii];
+    const Geo<R> geo(I);
+    PairK<R> P(I, step);        // constants of the instance of the pair in hand
+    int pinst = ii;
+    const bool own_fill = fill && P.noise;
+    const R own_lev = P.lev;
+    R fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0;
+    uint64_t mask = 0;          // ring positions holding this lane's pairs
+    unsigned head = 0, tail = 0;
+    __syncwarp();
+
+    // phase B + C on the ring positions [h0, h0 + cnt) (h0 a multiple of 32)
+    auto batch = [&](unsigned h0, int cnt) {
+        R g[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) g[c] = R(0);
+        if (lane < cnt) {
+            const unsigned p = (h0 + lane) & 63u;
+            const T4 rq = S.qr[p];
+            const int2 m = S.qm[p];
+            const int j = m.x, k = m.y >> 8, il = (m.y >> 1) & 31;
+            const bool rg = m.y & 1;
+            const int pi = S.hinst[il];
+            if (pi != pinst) {
+                P = PairK<R>(b.inst[pi], step);
+                pinst = pi;
+            }
+            const T4 Bi = S.hB[il], Ci = S.hC[il], Di = S.hD[il];
+            const T4 Bj = Bm[j], Cj = Cm[j], Dj = Dm[j];
+            const long long at = (long long)k * Np + base + il;
+            Z6<R> z;
+            int zmode = 0;
+            if (REUSE && P.noise && !rg) {
+                const T4 za = zA[at];
+                const T2 zb = zB[at];
+                if (!isnan(za.x)) {
+                    z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
+                    zmode = 1;
+                }
+            }
+            R ox, oy, oz, ce, ex, ey, ez, q, om;
+            sdpd_pair<R>(P, rq.x, rq.y, rq.z, rq.w, Bi, Ci, Di, Bj, Cj, Dj, !rg, zmode, z, ox, oy, oz, ce, ex, ey,
+                         ez, q, om);
+            if (!REUSE && fill && P.noise && !rg) {
+                T4 zw;
+                zw.x = z.z0; zw.y = z.z1; zw.z = z.z2; zw.w = z.z3;
+                T2 zv;
+                zv.x = z.z4; zv.y = z.z5;
+                zA[at] = zw;
+                zB[at] = zv;
+            }
+            pair_fh(ox, oy, oz, ce, ex, ey, ez, g[0], g[1], g[2], g[3], g[4], g[5]);
+            if (rg) {
+                R rcx, rcy, rcz;
+                rxn_of(b, j, rcx, rcy, rcz);
+                const R W = drag_weight(P, q, om);
+                g[6] = mul_rn(rcx, W);
+                g[7] = mul_rn(rcy, W);
+                g[8] = mul_rn(rcz, W);
+            }
+#pragma unroll
+            for (int c = 0; c < 9; ++c) S.res[lane * 9 + c] = g[c];
+        }
+        __syncwarp();
+        // phase C: this lane's pairs of the batch, in ring (= list) order
+        const unsigned off = h0 & 63u;
+        uint32_t mm = (uint32_t)(mask >> off) & (cnt == 32 ? FULL : ((1u << cnt) - 1u));
+        mask &= ~((uint64_t)mm << off);
+        while (mm) {
+            const int q = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const R *rr = S.res + q * 9;
+            // a zero drag-reaction term (non-sphere partner) leaves f unchanged exactly
+            fx = sub_rn(fx, rr[6]);
+            fy = sub_rn(fy, rr[7]);
+            fz = sub_rn(fz, rr[8]);
+            fx = add_rn(fx, rr[0]);
+            fy = add_rn(fy, rr[1]);
+            fz = add_rn(fz, rr[2]);
+            tx = add_rn(tx, rr[3]);
+            ty = add_rn(ty, rr[4]);
+            tz = add_rn(tz, rr[5]);
+        }
+        __syncwarp();
+    };
+
+    // phase A: the lists in step, the next entry prefetched
+    const int kmax = __reduce_max_sync(FULL, n);
+    int jn = n > 0 ? __ldg(b.nbr + s) : 0;
+    int jnn = n > 1 ? __ldg(b.nbr + Np + s) : 0;
+    T4 An;
+    if (n > 0) An = A[jn];
+    for (int k = 0; k < kmax; ++k) {
+        bool want = false, rig = false;
+        int j = 0;
+        R rx = 0, ry = 0, rz = 0, r2 = 0;
+        if (k < n) {
+            j = jn;
+            const T4 Aj = An;
+            if (k + 1 < n) {
+                jn = jnn;
+                An = A[jn];
+                if (k + 2 < n) jnn = __ldg(b.nbr + (long long)(k + 2) * Np + s);
+            }
+            rig = mir_type(Aj) == T_RIGID;
+            want = Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2);
+            if (!want && !REUSE && own_fill && !rig) {
+                T4 nm;
+                nm.x = R(NAN); nm.y = R(0); nm.z = R(0); nm.w = R(0);
+                zA[(long long)k * Np + s] = nm;
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL, want);
+        if (want) {
+            const unsigned pos = (tail + __popc(bal & below)) & 63u;
+            T4 rq;
+            rq.x = rx; rq.y = ry; rq.z = rz; rq.w = r2;
+            S.qr[pos] = rq;
+            S.qm[pos] = make_int2(j, (k << 8) | (lane << 1) | (rig ? 1 : 0));
+            mask |= 1ull << pos;
+        }
+        tail += __popc(bal);
+        if (tail - head >= 32u) {
+            __syncwarp();
+            batch(head, 32);
+            head += 32;
+        }
+    }
+    if (tail != head) {   // fewer than 32 left
+        __syncwarp();
+        batch(head, (int)(tail - head));
+    }
+    if (mine) write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, own_lev);
+    __syncwarp();   // the smem of this group is reused by the next one
+}
+
+// MINB: resident 256-thread blocks per SM the registers are capped for (2:
+// up to 128 registers, 16 warps; 3: 80 registers, 24 warps, a few spilled)
+template <class R, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_force_stream(Bufs b, int velver)
+{
+    extern __shared__ __align__(32) unsigned char stream_smem[];
+    StreamSmem<R> &S = reinterpret_cast<StreamSmem<R> *>(stream_smem)[threadIdx.x >> 5];
+    const uint32_t step = (uint32_t)(*b.step);
+    const bool fill = b.use_cache && velver == 1;
+    const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
+                       *b.cache_step == *b.step;
+    // every warp reads the epochs before the first one is written below
+    __syncthreads();
+    if (fill && blockIdx.x == 0 && threadIdx.x == 0) {
+        *b.cache_epoch = *b.list_epoch;
+        *b.cache_step = *b.step;
+    }
+    if (reuse) {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_stream_group<R, true>(b, S, base, step, false);
+    } else {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_stream_group<R, false>(b, S, base, step, fill);
     }
 }
 
@@ -1491,12 +1718,52 @@ void launch_drag(const Bufs &b, int precision, cudaStream_t st)
 }
 
 
+template <class R>
+static size_t stream_smem_bytes(int block) { return (size_t)(block / 32) * sizeof(StreamSmem<R>); }
+
+void init_pair_kernels()
+{
+    // the pair-stream kernels' shared memory at the largest block (256)
+    cudaFuncSetAttribute(k_force_stream<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stream_smem_bytes<float>(256));
+    cudaFuncSetAttribute(k_force_stream<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stream_smem_bytes<float>(256));
+    cudaFuncSetAttribute(k_force_stream<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stream_smem_bytes<double>(256));
+}
+
+template <class K>
+static unsigned persistent_grid_smem(K kernel, int block, size_t smem, long long N)
+{
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long need = (N + block - 1) / block;
+    return (unsigned)std::min<long long>(need, (long long)nsm * per_sm);
+}
+
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st)
 {
     if (!b.N) return;
     const int bs = b.pair_block;
     cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
-    if (newton3) {
+    if (newton3 >= 2) {
+        if (precision == SDPD_PREC_SPLIT) {
+            const size_t sm = stream_smem_bytes<float>(bs);
+            if (newton3 == 3)
+                k_force_stream<float, 3>
+                    <<<persistent_grid_smem(k_force_stream<float, 3>, bs, sm, b.N), bs, sm, st>>>(b, velver);
+            else
+                k_force_stream<float, 2>
+                    <<<persistent_grid_smem(k_force_stream<float, 2>, bs, sm, b.N), bs, sm, st>>>(b, velver);
+        } else {
+            const size_t sm = stream_smem_bytes<double>(bs);
+            k_force_stream<double, 1>
+                <<<persistent_grid_smem(k_force_stream<double, 1>, bs, sm, b.N), bs, sm, st>>>(b, velver);
+        }
+    } else if (newton3) {
         if (precision == SDPD_PREC_SPLIT) {
             k_force_half<float><<<persistent_grid(k_force_half<float>, bs, b.N), bs, 0, st>>>(b, velver);
             k_force_gather<float><<<nblk(b.N, bs), bs, 0, st>>>(b);

@@ -10,15 +10,23 @@ from paper_2002_03120_gb300 import autotune
 def test_search_picks_fastest_and_skips_nothing_required():
     times = {}
 
+    mode_cost = {1: 7.0, 0: 10.0, 2: 8.0, 3: 8.5}
+
     def fake(setting):
-        t = 10.0 - 3 * setting["newton3"] - 10 * setting["skin"] + abs(setting["block"] - 128) / 64
+        t = mode_cost[setting["newton3"]] - 10 * setting["skin"] + abs(setting["block"] - 128) / 64
         times[tuple(sorted(setting.items()))] = t
         return t
 
     best, table = autotune.search(fake)
     assert best == {"newton3": 1, "skin": 0.12, "block": 128}
     assert min(r["ms"] for r in table) == pytest.approx(fake(best))
-    assert any(r["newton3"] == 0 for r in table)
+    assert {r["newton3"] for r in table} == {0, 1, 2, 3}
+    # the pair stream is sampled at the two larger blocks and middle skins
+    assert {(r["block"], r["skin"]) for r in table if r["newton3"] == 2} == \
+        {(128, 0.03), (256, 0.03), (128, 0.06), (256, 0.06)}
+    # the three-block variant is FP32-only
+    _, t64 = autotune.search(fake, precision=0)
+    assert not any(r["newton3"] == 3 for r in t64)
 
 
 def test_search_ignores_unusable_settings():
@@ -42,10 +50,10 @@ def test_tune_on_gpu(tmp_path):
     from paper_2002_03120_gb300 import cases
     case = cases.sedimentation(nx=16, ny=16, nz=32)
     cache = str(tmp_path / "tune.json")
-    cand = {"newton3": (1, 0), "skin": (0.0, 0.06), "block": (128, 256)}
+    cand = {"newton3": (1, 0, 2), "skin": (0.0, 0.03, 0.06), "block": (128, 256)}
     best = autotune.tune(case, precision=B.SDPD_PREC_SPLIT, steps=3, warmup=2, cache_path=cache,
                          candidates=cand)
-    assert best["block"] in (128, 256) and best["newton3"] in (0, 1)
+    assert best["block"] in (128, 256) and best["newton3"] in (0, 1, 2)
     data = json.load(open(cache))
     (entry,) = data.values()
     assert all(r["ms"] is not None and r["ms"] > 0 for r in entry["table"])

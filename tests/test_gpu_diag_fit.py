@@ -55,7 +55,7 @@ def test_diagnostics_match_oracle(precision):
 
 
 def test_viscosity_fit_and_probe_match_oracle():
-    c = cases.poiseuille_meso(nx=8, ny=48, nz=8)
+    c = cases.poiseuille_meso(nx=12, ny=48, nz=12)   # periodic axes >= 3 h
     p = c["params"]
     mu, a, rho = p["eta"], p["body_amp"], p["rho0"]
     D = 0.5 * p["box"][1]

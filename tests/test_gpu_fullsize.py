@@ -34,8 +34,18 @@ def _sample(case, k, seed):
     return np.unique(idx.astype(np.int64))
 
 
+def _moving(case, seed, scale=1e-3):
+    """Seeded velocities and spins on the mobile particles, so that every
+    force term (and the spheres' torques) is non-zero."""
+    rng = np.random.default_rng(seed)
+    mob = (case["type"] <= 1)[:, None]
+    case["v"] = np.where(mob, rng.normal(0, scale, case["v"].shape), 0.0)
+    case["w"] = np.where(mob, rng.normal(0, scale / case["params"]["dx"], case["w"].shape), 0.0)
+    return case
+
+
 def test_dam_break_full_size_sampled_parity():
-    case = cases.dam_break()
+    case = _moving(cases.dam_break(), 3)
     sim = B.Sim(case, precision=B.SDPD_PREC_SPLIT)
     sim.step_count = 7
     sim.evaluate(1)
@@ -71,7 +81,7 @@ def test_dam_break_full_size_steps():
 
 
 def test_batched_viscometer_full_size():
-    insts = cases.viscometer_batch()
+    insts = [_moving(c, 100 + k) for k, c in enumerate(cases.viscometer_batch())]
     n = sum(len(c["x"]) for c in insts)
     assert n > 6_000_000
     sim = B.Sim(insts, precision=B.SDPD_PREC_SPLIT, max_neighbors=320)
