@@ -223,8 +223,12 @@ sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
  * 32 at a time, each particle summing its own in list order (forces equal to
  * those of 0 bit for bit); newton3 = 3 is that pass with its registers
  * capped for three 256-thread blocks per SM instead of two (a tuning choice;
- * FP32 pairs only, FP64 runs 2).  All give the same forces up to summation
- * order.
+ * FP32 pairs only, FP64 runs 2); newton3 = 4 is the Newton-3 pass with the
+ * owner writing each finished pair result (force, e x o) straight into the
+ * partner's column, which the partner then reads coalesced, as the FP64
+ * pass always does (for FP32 pairs, 1 keeps {o, ce} in the owner's column
+ * and the partner gathers it through the reverse index; 4 and 1 give the
+ * same bits).  All give the same forces up to summation order.
  * Invalidates the current neighbour build and graph.  Synchronous. */
 sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
 

@@ -22,10 +22,13 @@ import os
 from . import binding as B
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sdpd_gb300", "autotune.json")
-# force-pass variants (sdpd_set_force_mode): 1 Newton 3, 0 direct, 2 pair
-# stream (two 256-thread blocks per SM), 3 pair stream (three, FP32 only)
+# force-pass variants (sdpd_set_force_mode): 1 Newton 3, 4 Newton 3 with
+# pushed results (FP32 only; FP64 always pushes), 0 direct.  The pair-stream
+# variants 2 and 3 are not sampled by default: they measured slower than the
+# direct pass on every workload here (their shared-memory compaction buys
+# nothing where lanes are already busy, and costs L1 and instructions)
 CANDIDATES = {
-    "newton3": (1, 0, 2, 3),
+    "newton3": (1, 4, 0),
     "skin": (0.0, 0.03, 0.06, 0.12),
     "block": (64, 128, 256),
 }
@@ -60,12 +63,15 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
 
 
 def _sampled(setting, candidates, precision):
-    """Settings measured: the Newton-3 pass over the whole grid; the direct
-    pass at the default block (every skin) and without skin (every block);
-    the pair stream at the two larger blocks and the two middle skins, the
-    three-block variant for FP32 pairs only."""
+    """Settings measured: the Newton-3 passes over the whole grid (the push
+    variant for FP32 pairs only); the direct pass at the default block (every
+    skin) and without skin (every block); the pair stream, when asked for,
+    at the two larger blocks and the two middle skins, the three-block
+    variant for FP32 pairs only."""
     mode, skin, block = setting["newton3"], setting["skin"], setting["block"]
     skins = candidates["skin"]
+    if mode == 4 and precision == B.SDPD_PREC_FP64:
+        return False
     if mode == 0:
         return skin == skins[0] or block == 128
     if mode in (2, 3):

@@ -53,7 +53,8 @@ struct sdpd_ctx {
     Inst *d_inst = nullptr;
     int any_filter = 0, any_artvis = 0, any_reinit = 0;
     std::vector<double> probe_y;   // mean slab positions of the last viscosity probe
-    int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct, 2/3 pair stream
+    int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct, 2/3 pair stream,
+                                       // 4 half-pair with pushed results (FP32)
     int noise_cache = 1;               // second evaluation of a step reuses the first one's normals
     double skin = 0.03;                // Verlet skin as a fraction of h
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
@@ -382,10 +383,14 @@ sdpd_status ensure_geometry(sdpd_ctx *c)
     return SDPD_OK;
 }
 
+// force modes with the Newton-3 half-pair pass (1: pull gather in FP32,
+// 4: push); they need the reverse index of the lists
+inline bool half_pairs(int mode) { return mode == 1 || mode == 4; }
+
 void enqueue_build(sdpd_ctx *c, cudaStream_t st, const int *gate = nullptr)
 {
     c->b.use_cache = c->noise_cache;
-    launch_build(c->b, c->precision, c->newton3 == 1, gate, st);
+    launch_build(c->b, c->precision, half_pairs(c->newton3), gate, st);
 }
 
 }  // namespace
@@ -479,8 +484,8 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     {
         const size_t rs = (precision == SDPD_PREC_SPLIT) ? sizeof(float) : sizeof(double);
         const size_t Np = (size_t)c->Npad, own = (size_t)b.capown * Np, all = (size_t)c->cap * Np;
-        // the split path keeps {o, ce} in resA only
-        const size_t n_resA = 4 * rs * own, n_resB = precision == SDPD_PREC_SPLIT ? 0 : 2 * rs * own;
+        // {f, h.x} / {o, ce} in resA; {h.y, h.z} in resB (pushed results)
+        const size_t n_resA = 4 * rs * own, n_resB = 2 * rs * own;
         const size_t n_zA = 4 * rs * own, n_zB = 2 * rs * own;
         const size_t half_bytes = n_resA + n_resB + n_zA + n_zB, direct_bytes = 6 * rs * all;
         char *arena = nullptr, *oa = nullptr, *ob = nullptr, *dummy = nullptr;
@@ -775,7 +780,7 @@ sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
     (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->cells_valid) return fail(SDPD_E_STATE, "sdpd_build_cells must precede sdpd_compute_density");
-    launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, nullptr, (cudaStream_t)stream);
+    launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), nullptr, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     c->density_valid = true;
     return SDPD_OK;
@@ -835,7 +840,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         c->density_valid = false;
     }
     if (!c->density_valid) {
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, nullptr, st);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), nullptr, st);
         c->density_valid = true;
     }
     if (!c->graph) {
@@ -849,12 +854,12 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         // at velver 1 only after such a build, at velver 2 always
         cudaStream_t cs = c->cap_stream;
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, c->b.fresh, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), c->b.fresh, cs);
         launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 1, c->newton3, cs);
         launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), c->newton3 == 1, nullptr, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), nullptr, cs);
         launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 2, c->newton3, cs);
         launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);
@@ -875,7 +880,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
 sdpd_status sdpd_set_force_mode(sdpd_ctx *c, int newton3)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
-    if (newton3 < 0 || newton3 > 3) return fail(SDPD_E_INVALID, "force mode must be 0, 1, 2 or 3");
+    if (newton3 < 0 || newton3 > 4) return fail(SDPD_E_INVALID, "force mode must be 0, 1, 2, 3 or 4");
     CUDA_TRY(cudaDeviceSynchronize());
     if (newton3 != c->newton3) {
         c->newton3 = newton3;

@@ -1164,12 +1164,15 @@ __global__ void __launch_bounds__(256, MINB) k_force_stream(Bufs b, int velver)
 // six normals of each pair; the second reads them back, fetched one entry
 // ahead like the records, when the list has not been rebuilt in between (same
 // counter, so the same bits).
-template <class R, bool REUSE>
+// PUSH: the owner writes the finished pair result {f, e x o} into the
+// partner's column (FP64, and FP32 in force mode 4); otherwise (FP32, mode 1)
+// it keeps {o, ce} in its own column and the partner rebuilds f and e x o.
+// Both hand the partner the same bits.
+template <class R, bool REUSE, bool PUSH>
 __device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint32_t step, bool fill)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
-    constexpr bool PUSH = sizeof(R) == 8;
     if (s >= b.N) return;
     const int ti = b.stype[s];
     if (ti == T_RIGID) return;
@@ -1261,8 +1264,8 @@ __device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint
         R gx, gy, gz, hx, hy, hz;
         pair_fh(ox, oy, oz, ce, ex, ey, ez, gx, gy, gz, hx, hy, hz);
         T4 ra;
-        if constexpr (sizeof(R) == 4) {
-            // split path: {o, ce} (16 B); the partner rebuilds f and e x o
+        if constexpr (!PUSH) {
+            // {o, ce} (16 B); the partner rebuilds f and e x o
             ra.x = ox; ra.y = oy; ra.z = oz; ra.w = ce;
         } else {
             ra.x = gx; ra.y = gy; ra.z = gz; ra.w = hx;
@@ -1285,7 +1288,7 @@ __device__ __forceinline__ void force_half_slot(const Bufs &b, long long s, uint
 }
 
 // (FP32: at most 128 registers, so four 128-thread blocks fit on an SM)
-template <class R>
+template <class R, bool PUSH>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_force_half(Bufs b, int velver)
 {
     const uint32_t step = (uint32_t)(*b.step);
@@ -1301,10 +1304,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_force_half(Bufs
     // reuse is uniform over the launch
     if (reuse) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-            force_half_slot<R, true>(b, base + (threadIdx.x & 31), step, false);
+            force_half_slot<R, true, PUSH>(b, base + (threadIdx.x & 31), step, false);
     } else {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-            force_half_slot<R, false>(b, base + (threadIdx.x & 31), step, fill);
+            force_half_slot<R, false, PUSH>(b, base + (threadIdx.x & 31), step, fill);
     }
 }
 
@@ -1315,12 +1318,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_force_half(Bufs
 // reaction Eq. F_fpi_DG_reac), all in entry order + external force.  FP64
 // results were written into this particle's column (read coalesced); split
 // results are read from the owner's column through the reverse index.
-template <class R>
+template <class R, bool PUSH>
 __global__ void __launch_bounds__(256) k_force_gather(Bufs b)
 {
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
-    constexpr bool PUSH = sizeof(R) == 8;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.N) return;
     if (b.stype[s] != T_FLUID) return;
@@ -1749,7 +1751,7 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
     if (!b.N) return;
     const int bs = b.pair_block;
     cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
-    if (newton3 >= 2) {
+    if (newton3 == 2 || newton3 == 3) {
         if (precision == SDPD_PREC_SPLIT) {
             const size_t sm = stream_smem_bytes<float>(bs);
             if (newton3 == 3)
@@ -1764,12 +1766,15 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
                 <<<persistent_grid_smem(k_force_stream<double, 1>, bs, sm, b.N), bs, sm, st>>>(b, velver);
         }
     } else if (newton3) {
-        if (precision == SDPD_PREC_SPLIT) {
-            k_force_half<float><<<persistent_grid(k_force_half<float>, bs, b.N), bs, 0, st>>>(b, velver);
-            k_force_gather<float><<<nblk(b.N, bs), bs, 0, st>>>(b);
+        if (precision == SDPD_PREC_SPLIT && newton3 == 4) {
+            k_force_half<float, true><<<persistent_grid(k_force_half<float, true>, bs, b.N), bs, 0, st>>>(b, velver);
+            k_force_gather<float, true><<<nblk(b.N, bs), bs, 0, st>>>(b);
+        } else if (precision == SDPD_PREC_SPLIT) {
+            k_force_half<float, false><<<persistent_grid(k_force_half<float, false>, bs, b.N), bs, 0, st>>>(b, velver);
+            k_force_gather<float, false><<<nblk(b.N, bs), bs, 0, st>>>(b);
         } else {
-            k_force_half<double><<<persistent_grid(k_force_half<double>, bs, b.N), bs, 0, st>>>(b, velver);
-            k_force_gather<double><<<nblk(b.N, bs), bs, 0, st>>>(b);
+            k_force_half<double, true><<<persistent_grid(k_force_half<double, true>, bs, b.N), bs, 0, st>>>(b, velver);
+            k_force_gather<double, true><<<nblk(b.N, bs), bs, 0, st>>>(b);
         }
     } else if (precision == SDPD_PREC_SPLIT) {
         k_force_fluid<float><<<persistent_grid(k_force_fluid<float>, bs, b.N), bs, 0, st>>>(b, velver);

@@ -1,10 +1,13 @@
-"""The pair-stream force pass (force modes 2 and 3: the direct pass with the
-pairs within h compacted through shared memory and evaluated 32 at a time)
-adds the same terms in the same order as the direct pass (mode 0), so whole
-trajectories agree bit for bit: both sub-steps, the normals cache filled at
-velver 1 and read back at velver 2, fluid-sphere pairs with the drag
-reaction, walls, and several instances in one context.  Both also match the
-oracle within the force tolerance."""
+"""Force-pass variants that must agree bit for bit over whole trajectories
+(both sub-steps, the normals cache filled at velver 1 and read back at velver
+2, fluid-sphere pairs with the drag reaction, walls, several instances in one
+context):
+* the pair stream (modes 2 and 3: the direct pass with the pairs within h
+  compacted through shared memory and evaluated 32 at a time) adds the same
+  terms in the same order as the direct pass (mode 0);
+* the Newton-3 pass with pushed results (mode 4) hands the partner the same
+  bits as the one whose partner rebuilds them (mode 1).
+Each also matches the oracle within the force tolerance."""
 import numpy as np
 import pytest
 
@@ -38,7 +41,7 @@ CASES = {
     "sediment_small": lambda: cases.sedimentation(nx=12, ny=12, nz=24),
     "dambreak_small": lambda: cases.dam_break(scale=0.15, n_spheres=40),
     "slurry_batch": lambda: [cases.viscometer_instance(6000, 0.2, 300.0, 1e-2, seed=9, mesoscale=True),
-                             cases.viscometer_instance(3000, 0.1, 330.0, 1e-2, seed=3, mesoscale=True)],
+                             cases.viscometer_instance(5000, 0.1, 330.0, 1e-2, seed=3, mesoscale=True)],
 }
 
 
@@ -57,22 +60,24 @@ def _run(insts, precision, mode, cache=True, steps=3):
 @pytest.mark.parametrize("cache", [True, False])
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_pair_stream_equals_direct_bit_for_bit(name, precision, cache):
+def test_equal_variants_bit_for_bit(name, precision, cache):
     made = CASES[name]()
     insts = [_moving(c, 7 + k) for k, c in enumerate(made if isinstance(made, list) else [made])]
-    ref = _run(insts, precision, 0, cache)
-    for mode in (2, 3):
-        got = _run(insts, precision, mode, cache)
-        for a, b in zip(got, ref):
-            for q in ("x", "v", "w", "F", "N"):
-                assert np.array_equal(a[q], b[q]), (mode, q)
+    for ref_mode, modes in ((0, (2, 3)), (1, (4,))):
+        ref = _run(insts, precision, ref_mode, cache)
+        for mode in modes:
+            got = _run(insts, precision, mode, cache)
+            for a, b in zip(got, ref):
+                for q in ("x", "v", "w", "F", "N"):
+                    assert np.array_equal(a[q], b[q]), (ref_mode, mode, q)
 
 
+@pytest.mark.parametrize("mode", [2, 4])
 @pytest.mark.parametrize("precision", PRECISIONS)
-def test_pair_stream_matches_oracle(precision):
+def test_variants_match_oracle(precision, mode):
     case = _moving(cases.dam_break(scale=0.15, n_spheres=40), 12)
     sim = B.Sim(case, precision=precision)
-    sim.set_force_mode(2)
+    sim.set_force_mode(mode)
     sim.step_count = 6
     sim.evaluate(1)
     g = sim.state()
