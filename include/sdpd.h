@@ -228,7 +228,10 @@ sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
  * partner's column, which the partner then reads coalesced, as the FP64
  * pass always does (for FP32 pairs, 1 keeps {o, ce} in the owner's column
  * and the partner gathers it through the reverse index; 4 and 1 give the
- * same bits).  All give the same forces up to summation order.
+ * same bits); newton3 = 5 is the direct pass with only the list index and
+ * the partner's position fetched ahead, which needs fewer registers and runs
+ * more warps per SM (FP32 pairs; FP64 runs 0; the same bits as 0).  All give
+ * the same forces up to summation order.
  * Invalidates the current neighbour build and graph.  Synchronous. */
 sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
 

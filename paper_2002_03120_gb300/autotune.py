@@ -22,13 +22,14 @@ import os
 from . import binding as B
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sdpd_gb300", "autotune.json")
-# force-pass variants (sdpd_set_force_mode): 1 Newton 3, 4 Newton 3 with
-# pushed results (FP32 only; FP64 always pushes), 0 direct.  The pair-stream
-# variants 2 and 3 are not sampled by default: they measured slower than the
-# direct pass on every workload here (their shared-memory compaction buys
-# nothing where lanes are already busy, and costs L1 and instructions)
+# force-pass variants (sdpd_set_force_mode): 1 Newton 3, 0 direct, 5 direct
+# with fewer registers (FP32 only).  Not sampled by default, because they
+# measured slower on every workload here: 2 and 3 (the pair stream: its
+# shared-memory compaction buys nothing where lanes are already busy, and
+# costs L1 and instructions) and 4 (Newton 3 with pushed results: the
+# scattered stores cost more than the coalesced gather saves)
 CANDIDATES = {
-    "newton3": (1, 4, 0),
+    "newton3": (1, 0, 5),
     "skin": (0.0, 0.03, 0.06, 0.12),
     "block": (64, 128, 256),
 }
@@ -65,13 +66,16 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
 def _sampled(setting, candidates, precision):
     """Settings measured: the Newton-3 passes over the whole grid (the push
     variant for FP32 pairs only); the direct pass at the default block (every
-    skin) and without skin (every block); the pair stream, when asked for,
+    skin) and without skin (every block), its lean form (FP32 only, 128
+    threads) at the three smaller skins; the pair stream, when asked for,
     at the two larger blocks and the two middle skins, the three-block
     variant for FP32 pairs only."""
     mode, skin, block = setting["newton3"], setting["skin"], setting["block"]
     skins = candidates["skin"]
-    if mode == 4 and precision == B.SDPD_PREC_FP64:
+    if mode in (4, 5) and precision == B.SDPD_PREC_FP64:
         return False
+    if mode == 5:
+        return block == 128 and skin in skins[:3]
     if mode == 0:
         return skin == skins[0] or block == 128
     if mode in (2, 3):

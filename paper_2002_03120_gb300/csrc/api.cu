@@ -54,7 +54,8 @@ struct sdpd_ctx {
     int any_filter = 0, any_artvis = 0, any_reinit = 0;
     std::vector<double> probe_y;   // mean slab positions of the last viscosity probe
     int newton3 = 1;                   // force pass: 1 half-pair (Newton 3), 0 direct, 2/3 pair stream,
-                                       // 4 half-pair with pushed results (FP32)
+                                       // 4 half-pair with pushed results (FP32), 5 direct with
+                                       // fewer registers (FP32)
     int noise_cache = 1;               // second evaluation of a step reuses the first one's normals
     double skin = 0.03;                // Verlet skin as a fraction of h
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
@@ -880,7 +881,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
 sdpd_status sdpd_set_force_mode(sdpd_ctx *c, int newton3)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
-    if (newton3 < 0 || newton3 > 4) return fail(SDPD_E_INVALID, "force mode must be 0, 1, 2, 3 or 4");
+    if (newton3 < 0 || newton3 > 5) return fail(SDPD_E_INVALID, "force mode must be in 0..5");
     CUDA_TRY(cudaDeviceSynchronize());
     if (newton3 != c->newton3) {
         c->newton3 = newton3;

@@ -269,9 +269,11 @@ template <> struct Geo<float> {
     bool p0, p1, p2;
     int n0, n1, n2;
     float c0, c1, c2;
+    float glo, ghi;   // r^2 guard band (copied: a store in a pair loop may not
+                      // force them to be reloaded from the instance table)
     __device__ __forceinline__ explicit Geo(const Inst &I)
         : p0(I.periodic[0]), p1(I.periodic[1]), p2(I.periodic[2]), n0(I.nc[0]), n1(I.nc[1]),
-          n2(I.nc[2]), c0(I.csf[0]), c1(I.csf[1]), c2(I.csf[2]) {}
+          n2(I.nc[2]), c0(I.csf[0]), c1(I.csf[1]), c2(I.csf[2]), glo(I.guard_lo), ghi(I.guard_hi) {}
     __device__ __forceinline__ void disp(const float4 &Ai, const float4 &Aj, float &rx, float &ry,
                                          float &rz) const
     {
@@ -298,10 +300,11 @@ template <> struct Geo<double> {
     bool p0, p1, p2;
     double L0, L1, L2;
     unsigned long long h0, h1, h2;   // bits of L/2
+    double rc2;                      // h^2 (copied, as the guard band of the FP32 form)
     __device__ __forceinline__ explicit Geo(const Inst &I)
         : p0(I.periodic[0]), p1(I.periodic[1]), p2(I.periodic[2]), L0(I.box[0]), L1(I.box[1]),
           L2(I.box[2]), h0(abs_bits(0.5 * I.box[0])), h1(abs_bits(0.5 * I.box[1])),
-          h2(abs_bits(0.5 * I.box[2])) {}
+          h2(abs_bits(0.5 * I.box[2])), rc2(I.rc2) {}
     // minimum image: d - L if d > L/2, d + L if d < -L/2 (the same operations
     // as the oracle; the rare wrap is a branch)
     __device__ __forceinline__ static double img(double d, bool p, double L, unsigned long long hb)

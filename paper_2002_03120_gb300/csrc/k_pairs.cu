@@ -103,8 +103,8 @@ template <> struct Rel<float> {
     {
         geo.disp(Ai, Aj, rx, ry, rz);
         r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < I.guard_lo) return true;
-        if (r2 > I.guard_hi) return false;
+        if (r2 < geo.glo) return true;
+        if (r2 > geo.ghi) return false;
         return exact_within(b, I, gi, b.perm[j]);
     }
 };
@@ -115,7 +115,7 @@ template <> struct Rel<double> {
     {
         geo.disp(Ai, Aj, rx, ry, rz);
         r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
-        return abs_bits(r2) < abs_bits(I.rc2);   // r2 >= 0: the bit order is the value order
+        return abs_bits(r2) < abs_bits(geo.rc2);   // r2 >= 0: the bit order is the value order
     }
 };
 
@@ -184,6 +184,27 @@ __device__ __forceinline__ void finalize_slot(const Bufs &b, long long s, double
     D[s] = o;
 }
 
+// Streaming accesses (evict-first in L2): the neighbour lists and the normals
+// cache are each read or written once per pass and would otherwise push the
+// particle records, which every list revisits, out of L2.
+__device__ __forceinline__ int ld_stream(const int *p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_stream(const float2 *p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ld_stream(const double2 *p) { return __ldcs(p); }
+__device__ __forceinline__ double4_32a ld_stream(const double4_32a *p)
+{
+    const double2 a = __ldcs((const double2 *)p), b = __ldcs((const double2 *)p + 1);
+    return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_stream(float4 *p, float4 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(float2 *p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(double2 *p, double2 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(double4_32a *p, double4_32a v)
+{
+    __stcs((double2 *)p, make_double2(v.x, v.y));
+    __stcs((double2 *)p + 1, make_double2(v.z, v.w));
+}
+
 // Persistent pair kernels: each warp takes the next 32 slots from a counter
 // (zeroed before the launch) until none are left, so that no SM idles in the
 // tail of a partial last wave.  The result of a slot does not depend on
@@ -208,8 +229,8 @@ __device__ __forceinline__ void for_each_entry(const int *__restrict__ nb, long 
                                                const T4 *__restrict__ A, const double *__restrict__ side, F &&f)
 {
     if (n <= 0) return;
-    uint32_t en = (uint32_t)__ldg(nb);
-    uint32_t enn = n > 1 ? (uint32_t)__ldg(nb + Np) : 0u;
+    uint32_t en = (uint32_t)ld_stream(nb);
+    uint32_t enn = n > 1 ? (uint32_t)ld_stream(nb + Np) : 0u;
     T4 An = A[en & ~NB_FAR];
     double Sn = side ? side[en & ~NB_FAR] : 0.0;
     for (int k = 0; k < n; ++k) {
@@ -220,7 +241,7 @@ __device__ __forceinline__ void for_each_entry(const int *__restrict__ nb, long 
             en = enn;
             An = A[en & ~NB_FAR];
             if (side) Sn = side[en & ~NB_FAR];
-            if (k + 2 < n) enn = (uint32_t)__ldg(nb + (long long)(k + 2) * Np);
+            if (k + 2 < n) enn = (uint32_t)ld_stream(nb + (long long)(k + 2) * Np);
         }
         f(k, e, Aj, Sj);
     }
@@ -846,12 +867,12 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
     R fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0;
     const int n = b.ncnt[s];
     const long long Np = b.Npad;
-    int jn = n > 0 ? __ldg(nb) : 0;
-    int jnn = n > 1 ? __ldg(nb + Np) : 0;
+    int jn = n > 0 ? ld_stream(nb) : 0;
+    int jnn = n > 1 ? ld_stream(nb + Np) : 0;
     T4 An = A[jn], Bn = Bm[jn], Cn = Cm[jn], Dn = Dm[jn];
     T4 zan;
     T2 zbn;
-    if (REUSE && P.noise && n > 0) { zan = zA[s]; zbn = zB[s]; }
+    if (REUSE && P.noise && n > 0) { zan = ld_stream(zA + s); zbn = ld_stream(zB + s); }
     for (int k = 0; k < n; ++k) {
         const int j = jn;
         const T4 Aj = An, Bj = Bn, Cj = Cn, Dj = Dn;
@@ -862,10 +883,10 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
             jn = jnn;
             An = A[jn]; Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn];
             if (REUSE && P.noise) {
-                zan = zA[(long long)(k + 1) * Np + s];
-                zbn = zB[(long long)(k + 1) * Np + s];
+                zan = ld_stream(zA + (long long)(k + 1) * Np + s);
+                zbn = ld_stream(zB + (long long)(k + 1) * Np + s);
             }
-            if (k + 2 < n) jnn = __ldg(nb + (long long)(k + 2) * Np);
+            if (k + 2 < n) jnn = ld_stream(nb + (long long)(k + 2) * Np);
         }
         const bool rig = mir_type(Aj) == T_RIGID;
         const long long at = (long long)k * Np + s;
@@ -874,7 +895,7 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
             if (!REUSE && fill && !rig) {
                 T4 nm;
                 nm.x = R(NAN); nm.y = R(0); nm.z = R(0); nm.w = R(0);
-                zA[at] = nm;
+                st_stream(zA + at, nm);
             }
             continue;
         }
@@ -893,8 +914,8 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
             zw.x = z.z0; zw.y = z.z1; zw.z = z.z2; zw.w = z.z3;
             T2 zv;
             zv.x = z.z4; zv.y = z.z5;
-            zA[at] = zw;
-            zB[at] = zv;
+            st_stream(zA + at, zw);
+            st_stream(zB + at, zv);
         }
         // every accumulation step rounded explicitly (the pair-stream pass
         // adds the same terms in the same order and must match bit for bit)
@@ -917,6 +938,128 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
         tz = add_rn(tz, hz);
     }
     write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, P.lev);
+}
+
+template <class R, bool REUSE>
+__device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s, uint32_t step, bool fill)
+{
+    using T4 = typename Vec<R>::T4;
+    using T2 = typename Vec2<R>::T2;
+    if (s >= b.N) return;
+    if (b.stype[s] != T_FLUID) return;
+    const int gi = b.perm[s];
+    const Inst &I = b.inst[b.pinst[gi]];
+    const Geo<R> geo(I);
+    const PairK<R> P(I, step);
+    fill = fill && P.noise;
+    const T4 *__restrict__ A = Mir<R>::A(b);
+    const T4 *__restrict__ Bm = Mir<R>::B(b);
+    const T4 *__restrict__ Cm = Mir<R>::C(b);
+    const T4 *__restrict__ Dm = Mir<R>::D(b);
+    T4 *__restrict__ zA = (T4 *)b.zdA;
+    T2 *__restrict__ zB = (T2 *)b.zdB;
+    const int *__restrict__ nb = b.nbr + s;
+    const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
+    R fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0;
+    const int n = b.ncnt[s];
+    const long long Np = b.Npad;
+    int jn = n > 0 ? ld_stream(nb) : 0;
+    int jnn = n > 1 ? ld_stream(nb + Np) : 0;
+    T4 An = A[jn];
+    T4 zan;
+    T2 zbn;
+    if (REUSE && P.noise && n > 0) { zan = ld_stream(zA + s); zbn = ld_stream(zB + s); }
+    for (int k = 0; k < n; ++k) {
+        const int j = jn;
+        const T4 Aj = An;
+        T4 za;
+        T2 zb;
+        if (REUSE) { za = zan; zb = zbn; }
+        if (k + 1 < n) {
+            jn = jnn;
+            An = A[jn];
+            if (REUSE && P.noise) {
+                zan = ld_stream(zA + (long long)(k + 1) * Np + s);
+                zbn = ld_stream(zB + (long long)(k + 1) * Np + s);
+            }
+            if (k + 2 < n) jnn = ld_stream(nb + (long long)(k + 2) * Np);
+        }
+        const bool rig = mir_type(Aj) == T_RIGID;
+        const long long at = (long long)k * Np + s;
+        R rx, ry, rz, r2;
+        if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) {
+            if (!REUSE && fill && !rig) {
+                T4 nm;
+                nm.x = R(NAN); nm.y = R(0); nm.z = R(0); nm.w = R(0);
+                st_stream(zA + at, nm);
+            }
+            continue;
+        }
+        const T4 Bj = Bm[j], Cj = Cm[j], Dj = Dm[j];
+        R ox, oy, oz, ce, ex, ey, ez, q, om;
+        Z6<R> z;
+        int zmode = 0;
+        // an entry beyond h in the first evaluation carries the NaN marker
+        if (REUSE && P.noise && !rig && !isnan(za.x)) {
+            z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
+            zmode = 1;
+        }
+        sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, !rig, zmode, z, ox, oy, oz, ce, ex, ey, ez,
+                     q, om);
+        if (!REUSE && fill && !rig) {
+            T4 zw;
+            zw.x = z.z0; zw.y = z.z1; zw.z = z.z2; zw.w = z.z3;
+            T2 zv;
+            zv.x = z.z4; zv.y = z.z5;
+            st_stream(zA + at, zw);
+            st_stream(zB + at, zv);
+        }
+        // every accumulation step rounded explicitly (the pair-stream pass
+        // adds the same terms in the same order and must match bit for bit)
+        R gx, gy, gz, hx, hy, hz;
+        pair_fh(ox, oy, oz, ce, ex, ey, ez, gx, gy, gz, hx, hy, hz);
+        if (rig) {
+            // Eq. F_fpi_DG_reac: -F^DG_s W_sj / S_s
+            R rcx, rcy, rcz;
+            rxn_of(b, j, rcx, rcy, rcz);
+            const R W = drag_weight(P, q, om);
+            fx = sub_rn(fx, mul_rn(rcx, W));
+            fy = sub_rn(fy, mul_rn(rcy, W));
+            fz = sub_rn(fz, mul_rn(rcz, W));
+        }
+        fx = add_rn(fx, gx);
+        fy = add_rn(fy, gy);
+        fz = add_rn(fz, gz);
+        tx = add_rn(tx, hx);
+        ty = add_rn(ty, hy);
+        tz = add_rn(tz, hz);
+    }
+    write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, P.lev);
+}
+
+// The direct pass with only the list index and the partner's position
+// fetched ahead (its other records are loaded after the r < h decision):
+// fewer registers, so more warps per SM hide the loads instead (force mode
+// 5; the same terms in the same order, so the same bits as force_fluid_slot).
+template <class R, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_force_fluid_lean(Bufs b, int velver)
+{
+    const uint32_t step = (uint32_t)(*b.step);
+    const bool fill = b.use_cache && velver == 1;
+    const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
+                       *b.cache_step == *b.step;
+    __syncthreads();
+    if (fill && blockIdx.x == 0 && threadIdx.x == 0) {
+        *b.cache_epoch = *b.list_epoch;
+        *b.cache_step = *b.step;
+    }
+    if (reuse) {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_fluid_slot_lean<R, true>(b, base + (threadIdx.x & 31), step, false);
+    } else {
+        for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
+            force_fluid_slot_lean<R, false>(b, base + (threadIdx.x & 31), step, fill);
+    }
 }
 
 template <class R>
@@ -1765,7 +1908,7 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
             k_force_stream<double, 1>
                 <<<persistent_grid_smem(k_force_stream<double, 1>, bs, sm, b.N), bs, sm, st>>>(b, velver);
         }
-    } else if (newton3) {
+    } else if (newton3 == 1 || newton3 == 4) {
         if (precision == SDPD_PREC_SPLIT && newton3 == 4) {
             k_force_half<float, true><<<persistent_grid(k_force_half<float, true>, bs, b.N), bs, 0, st>>>(b, velver);
             k_force_gather<float, true><<<nblk(b.N, bs), bs, 0, st>>>(b);
@@ -1776,6 +1919,12 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
             k_force_half<double, true><<<persistent_grid(k_force_half<double, true>, bs, b.N), bs, 0, st>>>(b, velver);
             k_force_gather<double, true><<<nblk(b.N, bs), bs, 0, st>>>(b);
         }
+    } else if (newton3 == 5) {
+        // registers capped for five 128-thread blocks per SM (20 warps)
+        if (precision == SDPD_PREC_SPLIT)
+            k_force_fluid_lean<float, 5><<<persistent_grid(k_force_fluid_lean<float, 5>, 128, b.N), 128, 0, st>>>(b, velver);
+        else
+            k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b, velver);
     } else if (precision == SDPD_PREC_SPLIT) {
         k_force_fluid<float><<<persistent_grid(k_force_fluid<float>, bs, b.N), bs, 0, st>>>(b, velver);
     } else {

@@ -10,7 +10,7 @@ from paper_2002_03120_gb300 import autotune
 def test_search_picks_fastest_and_skips_nothing_required():
     times = {}
 
-    mode_cost = {1: 7.0, 4: 7.5, 0: 10.0, 2: 8.0, 3: 8.5}
+    mode_cost = {1: 7.0, 4: 7.5, 0: 10.0, 2: 8.0, 3: 8.5, 5: 9.0}
 
     def fake(setting):
         t = mode_cost[setting["newton3"]] - 10 * setting["skin"] + abs(setting["block"] - 128) / 64
@@ -20,16 +20,17 @@ def test_search_picks_fastest_and_skips_nothing_required():
     best, table = autotune.search(fake)
     assert best == {"newton3": 1, "skin": 0.12, "block": 128}
     assert min(r["ms"] for r in table) == pytest.approx(fake(best))
-    assert {r["newton3"] for r in table} == {0, 1, 4}
+    assert {r["newton3"] for r in table} == {0, 1, 5}
     # asked for, the pair stream is sampled at the two larger blocks and
     # middle skins
-    cand = dict(autotune.CANDIDATES, newton3=(1, 4, 0, 2, 3))
+    cand = dict(autotune.CANDIDATES, newton3=(1, 4, 0, 2, 3, 5))
     _, t32 = autotune.search(fake, cand, precision=1)
     assert {(r["block"], r["skin"]) for r in t32 if r["newton3"] == 2} == \
         {(128, 0.03), (256, 0.03), (128, 0.06), (256, 0.06)}
-    # the push variant and the three-block stream are FP32-only
+    # the push variant, the three-block stream and the lean direct pass are
+    # FP32-only
     _, t64 = autotune.search(fake, cand, precision=0)
-    assert not any(r["newton3"] in (3, 4) for r in t64)
+    assert not any(r["newton3"] in (3, 4, 5) for r in t64)
 
 
 def test_search_ignores_unusable_settings():

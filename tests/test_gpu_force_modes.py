@@ -3,8 +3,10 @@
 2, fluid-sphere pairs with the drag reaction, walls, several instances in one
 context):
 * the pair stream (modes 2 and 3: the direct pass with the pairs within h
-  compacted through shared memory and evaluated 32 at a time) adds the same
-  terms in the same order as the direct pass (mode 0);
+  compacted through shared memory and evaluated 32 at a time) and the lean
+  direct pass (mode 5: fewer registers, the partner's records loaded after
+  the r < h decision) add the same terms in the same order as the direct
+  pass (mode 0);
 * the Newton-3 pass with pushed results (mode 4) hands the partner the same
   bits as the one whose partner rebuilds them (mode 1).
 Each also matches the oracle within the force tolerance."""
@@ -63,7 +65,7 @@ def _run(insts, precision, mode, cache=True, steps=3):
 def test_equal_variants_bit_for_bit(name, precision, cache):
     made = CASES[name]()
     insts = [_moving(c, 7 + k) for k, c in enumerate(made if isinstance(made, list) else [made])]
-    for ref_mode, modes in ((0, (2, 3)), (1, (4,))):
+    for ref_mode, modes in ((0, (2, 3, 5)), (1, (4,))):
         ref = _run(insts, precision, ref_mode, cache)
         for mode in modes:
             got = _run(insts, precision, mode, cache)
@@ -72,7 +74,7 @@ def test_equal_variants_bit_for_bit(name, precision, cache):
                     assert np.array_equal(a[q], b[q]), (ref_mode, mode, q)
 
 
-@pytest.mark.parametrize("mode", [2, 4])
+@pytest.mark.parametrize("mode", [2, 4, 5])
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_variants_match_oracle(precision, mode):
     case = _moving(cases.dam_break(scale=0.15, n_spheres=40), 12)
