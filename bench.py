@@ -273,6 +273,19 @@ def time_plain_fp64(case, args, stream, flush):
     return dict(ms_per_step=tot_ms, pairs=pairs, steps=steps, instances=len(insts))
 
 
+def force_kernel_name(mode, split):
+    """The pair kernel that does the arithmetic of a force mode (the phase-1
+    kernel of the Newton-3 passes), as ncu names it."""
+    r = "float" if split else "double"
+    if mode in (1, 4):
+        return f"k_force_half<{r}, {'true' if mode == 4 or not split else 'false'}>"
+    if mode in (2, 3):
+        return f"k_force_stream<{r}, {mode if split else 1}>"
+    if mode == 5 and split:
+        return "k_force_fluid_lean<float, 5>"
+    return f"k_force_fluid<{r}>"
+
+
 def time_native(args, ws, rank, local):
     import torch
 
@@ -573,8 +586,7 @@ def main():
     cnt = ncu_counters({"sedimentation": "counters_sedimentation", "dambreak": "counters_dambreak",
                         "batch": "counters_batch"}.get(args.workload, "none"))
     integ_cnt = ncu_counters("counters_integrate").get(f"k_integrate<{'float' if split else 'double'}>", {})
-    n3 = (main_r.get("setting") or {}).get("newton3", 1)
-    main_k = f"{'k_force_half' if n3 else 'k_force_fluid'}<{'float' if split else 'double'}>"
+    main_k = force_kernel_name((main_r.get("setting") or {}).get("newton3", 1), split)
     # the force pass is bound by arithmetic issue: algorithmic flops = 160 per
     # unordered pair, against this GPU's measured FMA rate of the path's
     # precision (sdpd_alu_peaks, run at the start of this bench)

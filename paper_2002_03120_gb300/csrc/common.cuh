@@ -232,8 +232,22 @@ template <> struct BoxMuller<double> {
         z1 = __dmul_rn(rad, s);
     }
 };
-// FP32: the accurate logarithm (ln U1 -> 0 as U1 -> 1, where an absolute
-// error would swamp it), the radius as x rsqrt(x), and the angle
+// ln U of a uniform U = (m + 1/2) 2^-23 in FP32, from the hardware base-2
+// logarithm (absolute error about 2^-22 on [2^-24, 1)) where |ln U| >= 1/64,
+// and from the Taylor series of ln(1 - d) in the exact d = 1 - U below that,
+// where an absolute error would swamp the small logarithm: five terms leave
+// a truncation below d^6 / 6 < 2^-38.  The result carries a relative error
+// of a few 1e-7 at most over the whole range.
+__device__ __forceinline__ float bm_log_f32(float U)
+{
+    const float d = 1.0f - U;   // exact: U has at most 24 significant bits
+    const float ser = -d * fmaf(d, fmaf(d, fmaf(d, fmaf(d, 0.2f, 0.25f), 1.0f / 3.0f), 0.5f), 1.0f);
+    const float hw = __log2f(U) * 0.69314718055994531f;
+    return d < 0.015625f ? ser : hw;
+}
+
+// FP32: the logarithm above (ln U1 -> 0 as U1 -> 1, where an absolute error
+// would swamp it), the radius as x rsqrt(x), and the angle
 // 2 pi U2 = pi + 2 pi (U2 - 1/2) through the hardware sine and cosine on
 // [-pi, pi] (absolute error below 2^-21.4; cos(pi + t) = -cos t exactly).  A
 // normal is within about 5e-6 of the exact value (radius up to 5.8).
@@ -242,7 +256,7 @@ template <> struct BoxMuller<float> {
     {
         const float U1 = ((float)(ua >> 9) + 0.5f) * (1.0f / 8388608.0f);
         const float U2 = ((float)(ub >> 9) + 0.5f) * (1.0f / 8388608.0f);
-        const float m2l = -2.0f * logf(U1);   // > 0: U1 <= 1 - 2^-24
+        const float m2l = -2.0f * bm_log_f32(U1);   // > 0: U1 <= 1 - 2^-24
         const float rad = m2l * rsqrtf(m2l);
         float s, c;
         __sincosf(6.28318530717958648f * (U2 - 0.5f), &s, &c);
