@@ -261,6 +261,11 @@ sdpd_status prepare(sdpd_ctx *c)
         I.rb = rb;
         I.rb2 = rb * rb;
         I.half_skin = 0.5 * skin * h;
+        for (int a = 0; a < 3; ++a) {
+            I.dom_hi[a] = I.origin[a] + I.box[a];
+            const double hb = 0.5 * I.box[a];
+            std::memcpy(&I.hbox_bits[a], &hb, sizeof hb);
+        }
         I.rb2f = (float)(rb * rb * (1.0 + 1e-5));
         I.guard_lo = (float)(I.rc2 * (1.0 - 1e-5));
         I.guard_hi = (float)(I.rc2 * (1.0 + 1e-5));

@@ -58,6 +58,10 @@ struct Inst {
     // until a particle has moved skin h / 2 since the build
     double rb, rb2, half_skin;
     float rb2f;
+    // the update kernel's bounds: origin + box (as the oracle forms it) and
+    // the bits of box / 2, compared on the integer pipe
+    double dom_hi[3];
+    unsigned long long hbox_bits[3];
 };
 
 // Device buffers of a context (all device pointers).

@@ -41,10 +41,26 @@ __device__ __forceinline__ double div_rn(double a, double d, double y)
     return __fma_rn(r, y, q0);
 }
 
+// Comparisons on the integer pipe (the FP64 pipe of this part runs at 1/64 of
+// the FP32 rate and bounds the update): key(x) orders like x for every
+// non-NaN double, -0 and +0 alike; a NaN takes a branch the IEEE comparison
+// would not, but stays NaN and is flagged either way.
+__device__ __forceinline__ long long ord_key(double x)
+{
+    const long long k = __double_as_longlong(x);
+    return k >= 0 ? k : (long long)(0x8000000000000000ull - (unsigned long long)k);
+}
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
+}
+
 // Velocity Verlet (Eqs. newton1, newton2): v += dt/2 F/m, w += dt/2 N/I;
 // velver 1 also drifts x += dt v, wraps periodic axes and mirrors particles
 // that crossed a wall plane (normal velocity reversed).  The arithmetic is
-// written without fused multiply-adds so it repeats the oracle bit for bit.
+// written without fused multiply-adds so it repeats the oracle bit for bit;
+// the decisions (wrap, reflection, periodic jump, finiteness) are taken on
+// the integer pipe from the bit patterns, with the oracle's outcomes.
 template <class R>
 __global__ void k_integrate(Bufs b, int velver)
 {
@@ -56,36 +72,37 @@ __global__ void k_integrate(Bufs b, int velver)
     if (t != T_FLUID && t != T_RIGID) return;
     const Inst &I = b.inst[b.pinst[g]];
     const double im = b.m[g], iI = b.Iner[g], rm = b.rm[g], rI = b.rI[g];
+    const double hdt = I.hdt;
     double v[3], w[3], x[3];
-    bool bad = false;
+    bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        v[a] = __dadd_rn(b.v[3 * g + a], __dmul_rn(I.hdt, div_rn(b.F[3 * g + a], im, rm)));
-        w[a] = __dadd_rn(b.w[3 * g + a], __dmul_rn(I.hdt, div_rn(b.T[3 * g + a], iI, rI)));
+        v[a] = __dadd_rn(b.v[3 * g + a], __dmul_rn(hdt, div_rn(b.F[3 * g + a], im, rm)));
+        w[a] = __dadd_rn(b.w[3 * g + a], __dmul_rn(hdt, div_rn(b.T[3 * g + a], iI, rI)));
     }
     if (velver == 1) {
+        const double dt = I.dt;
         double dl[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double x0 = b.x[3 * g + a];
-            double xa = __dadd_rn(x0, __dmul_rn(I.dt, v[a]));
-            const double lo = I.origin[a], hi = __dadd_rn(I.origin[a], I.box[a]);
-            if (I.periodic[a]) {
-                if (xa < lo) xa = __dadd_rn(xa, I.box[a]);
-                else if (xa >= hi) xa = __dsub_rn(xa, I.box[a]);
+            double xa = __dadd_rn(x0, __dmul_rn(dt, v[a]));
+            const double lo = I.origin[a], hi = I.dom_hi[a], L = I.box[a];
+            const long long kx = ord_key(xa);
+            const bool per = I.periodic[a];
+            if (per) {
+                if (kx < ord_key(lo)) xa = __dadd_rn(xa, L);
+                else if (kx >= ord_key(hi)) xa = __dsub_rn(xa, L);
             } else {
-                if (xa < lo) { xa = __dadd_rn(lo, __dsub_rn(lo, xa)); v[a] = -v[a]; }
-                else if (xa > hi) { xa = __dsub_rn(hi, __dsub_rn(xa, hi)); v[a] = -v[a]; }
+                if (kx < ord_key(lo)) { xa = __dadd_rn(lo, __dsub_rn(lo, xa)); v[a] = -v[a]; }
+                else if (kx > ord_key(hi)) { xa = __dsub_rn(hi, __dsub_rn(xa, hi)); v[a] = -v[a]; }
             }
             x[a] = xa;
             b.x[3 * g + a] = xa;
-            bad |= !isfinite(xa);
-            // displacement without the periodic jump
-            double d = xa - x0;
-            if (I.periodic[a]) {
-                if (d > 0.5 * I.box[a]) d -= I.box[a];
-                else if (d < -0.5 * I.box[a]) d += I.box[a];
-            }
+            ok &= finite_bits(xa);
+            // displacement without the periodic jump (|d| > L/2 decided on the bits)
+            double d = __dsub_rn(xa, x0);
+            if (per && abs_bits(d) > I.hbox_bits[a]) d = (__double_as_longlong(d) > 0) ? __dsub_rn(d, L) : __dadd_rn(d, L);
             dl[a] = d;
         }
         // keep the mirrors of the unchanged slot order current: cell-relative
@@ -104,15 +121,15 @@ __global__ void k_integrate(Bufs b, int velver)
             a64.x = x[0]; a64.y = x[1]; a64.z = x[2];
             b.A64[s] = a64;
         }
-        if (ds.x * ds.x + ds.y * ds.y + ds.z * ds.z > I.half_skin * I.half_skin) *b.need_build = 1;
+        if (fma(ds.z, ds.z, fma(ds.y, ds.y, ds.x * ds.x)) > I.half_skin * I.half_skin) *b.need_build = 1;
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         b.v[3 * g + a] = v[a];
         b.w[3 * g + a] = w[a];
-        bad |= !isfinite(v[a]) || !isfinite(w[a]);
+        ok &= finite_bits(v[a]) & finite_bits(w[a]);
     }
-    if (bad) atomicOr(b.err, ERR_NONFINITE);
+    if (!ok) atomicOr(b.err, ERR_NONFINITE);
     write_vel_mirror<R>(b, s, v, w);
 }
 
