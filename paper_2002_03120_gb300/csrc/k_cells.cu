@@ -257,27 +257,12 @@ __global__ void k_neighbors(Bufs b, const int *gate)
     bool rig = false;
     uint32_t entry;
     int tj;
-    // cells whose box lies farther than rb from the particle hold no
-    // candidate within rb: skipped (corner cells about half the time, edge
-    // cells a fifth), with a margin far above the float rounding so the list
-    // is the same; rigid particles also list contacts beyond rb, so they
-    // scan every cell
-    const float cull2 = I.rb2f * 1.0001f;
-    const bool cull = ti != T_RIGID;
     for (int q = 0; q < 27; ++q) {
         const int code = adj[q];
         if (code < 0) break;
         const int key = code >> 5, oc = code & 31;
-        const int ox = oc % 3 - 1, oy = (oc / 3) % 3 - 1, oz = oc / 9 - 1;
-        if (cull) {
-            // gap to the cell's box, never negative (a particle clamped into
-            // a boundary cell may lie outside its own cell)
-            const float gx = fmaxf(0.f, ox > 0 ? I.csf[0] - Ai.x : (ox < 0 ? Ai.x : 0.f));
-            const float gy = fmaxf(0.f, oy > 0 ? I.csf[1] - Ai.y : (oy < 0 ? Ai.y : 0.f));
-            const float gz = fmaxf(0.f, oz > 0 ? I.csf[2] - Ai.z : (oz < 0 ? Ai.z : 0.f));
-            if (gx * gx + gy * gy + gz * gz > cull2) continue;
-        }
-        const float sx = (float)ox * I.csf[0], sy = (float)oy * I.csf[1], sz = (float)oz * I.csf[2];
+        const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
+                    sz = (float)(oc / 9 - 1) * I.csf[2];
         const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
         for (int j = j0; j < j1; ++j) {
             if (j == s || !nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) continue;
