@@ -248,6 +248,14 @@ sdpd_status sdpd_set_noise_cache(sdpd_ctx *ctx, int on);
  * Synchronous. */
 sdpd_status sdpd_set_block_size(sdpd_ctx *ctx, int threads);
 
+/* Lanes per particle of the direct force pass (force mode 0): 1 (default), 2
+ * or 4.  With more than one, the lanes of a particle take every tpp-th entry
+ * of its list and their sums are added by a fixed butterfly of shuffles, so
+ * small workloads fill more of the GPU; the result differs from tpp = 1 only
+ * by summation order and is the same on every run.  A tuning knob.
+ * Invalidates the current graph.  Synchronous. */
+sdpd_status sdpd_set_threads_per_particle(sdpd_ctx *ctx, int tpp);
+
 /* Verlet skin as a fraction of h (default 0.03): neighbour lists hold the
  * pairs within h (1 + skin) and are reused by later evaluations until some
  * particle has moved skin h / 2 since the build (decided on the device each

@@ -3,7 +3,8 @@
 For one workload (a list of instances and a precision) it times full steps
 under each candidate setting -- force-pass variant (Newton-3 half pairs,
 direct, or the pair stream through shared memory at two register caps),
-Verlet skin, pair-kernel block size -- picks the fastest, and keeps
+Verlet skin, pair-kernel block size, lanes per particle of the direct pass
+-- picks the fastest, and keeps
 the choice in a JSON file keyed by GPU name, precision and size class (total
 particles rounded to a power of two, number of instances), so later contexts
 of the same class reuse it without measuring again.
@@ -32,6 +33,7 @@ CANDIDATES = {
     "newton3": (1, 0, 5),
     "skin": (0.0, 0.03, 0.06, 0.12),
     "block": (64, 128, 256),
+    "tpp": (1, 2, 4),   # lanes per particle of the direct pass
 }
 
 
@@ -72,6 +74,10 @@ def _sampled(setting, candidates, precision):
     variant for FP32 pairs only."""
     mode, skin, block = setting["newton3"], setting["skin"], setting["block"]
     skins = candidates["skin"]
+    if setting.get("tpp", 1) != 1:
+        # several lanes per particle: the direct pass at the default block
+        # and the default skin
+        return mode == 0 and block == 128 and skin == skins[min(1, len(skins) - 1)]
     if mode in (4, 5) and precision == B.SDPD_PREC_FP64:
         return False
     if mode == 5:
@@ -105,6 +111,7 @@ def search(measure, candidates=CANDIDATES, precision=None):
 
 def apply(sim: "B.Sim", setting: dict) -> None:
     sim.set_force_mode(int(setting["newton3"]))
+    sim.set_threads_per_particle(int(setting.get("tpp", 1)))
     sim.set_skin(float(setting["skin"]))
     sim.set_block_size(int(setting["block"]))
 

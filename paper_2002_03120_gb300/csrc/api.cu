@@ -451,6 +451,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     b.cap = c->cap;
     b.K = c->K;
     b.pair_block = 128;
+    b.tpp = 1;
     auto cleanup = [&](sdpd_status s) {
         sdpd_destroy(c);
         return s;
@@ -916,6 +917,18 @@ sdpd_status sdpd_set_block_size(sdpd_ctx *c, int threads)
     CUDA_TRY(cudaDeviceSynchronize());
     if (threads != c->b.pair_block) {
         c->b.pair_block = threads;
+        drop_graph(c);
+    }
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_set_threads_per_particle(sdpd_ctx *c, int tpp)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (tpp != 1 && tpp != 2 && tpp != 4) return fail(SDPD_E_INVALID, "threads per particle must be 1, 2 or 4");
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (tpp != c->b.tpp) {
+        c->b.tpp = tpp;
         drop_graph(c);
     }
     return SDPD_OK;

@@ -69,6 +69,7 @@ struct Bufs {
     long long N, Npad;
     int n_inst, ncell_total, nrigid, cap, K;
     int pair_block;            // threads per block of the pair kernels (64, 128 or 256)
+    int tpp;                   // lanes per particle of the direct force pass (1, 2 or 4)
     const Inst *inst;          // [n_inst]
     // master state (gid order)
     double *x, *v, *w, *F, *T;

@@ -1298,6 +1298,147 @@ __global__ void __launch_bounds__(256, MINB) k_force_stream(Bufs b, int velver)
     }
 }
 
+// The direct pass with TPP lanes per particle (TPP = 2 or 4): the lanes of a
+// particle take the entries sub, sub + TPP, ... of its list (sub = lane %
+// TPP), each summing its share in list order, and a butterfly of shuffles
+// adds the TPP partial sums in a fixed order; the first lane writes.  Small
+// workloads so fill TPP times as many warps.
+template <class R, bool REUSE, int TPP>
+__device__ __forceinline__ void force_fluid_slot_tpp(const Bufs &b, long long s, int sub, uint32_t step, bool fill)
+{
+    using T4 = typename Vec<R>::T4;
+    using T2 = typename Vec2<R>::T2;
+    const bool active = s < b.N && b.stype[s] == T_FLUID;
+    R fx = 0, fy = 0, fz = 0, tx = 0, ty = 0, tz = 0;
+    int gi = 0;
+    const Inst *Ip = b.inst;
+    R lev = 0;
+    if (active) {
+        gi = b.perm[s];
+        const Inst &I = b.inst[b.pinst[gi]];
+        Ip = &I;
+        const Geo<R> geo(I);
+        const PairK<R> P(I, step);
+        lev = P.lev;
+        const bool fl = fill && P.noise;
+        const T4 *__restrict__ A = Mir<R>::A(b);
+        const T4 *__restrict__ Bm = Mir<R>::B(b);
+        const T4 *__restrict__ Cm = Mir<R>::C(b);
+        const T4 *__restrict__ Dm = Mir<R>::D(b);
+        T4 *__restrict__ zA = (T4 *)b.zdA;
+        T2 *__restrict__ zB = (T2 *)b.zdB;
+        const int *__restrict__ nb = b.nbr + s;
+        const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
+        const int n = b.ncnt[s];
+        const long long Np = b.Npad;
+        int jn = sub < n ? ld_stream(nb + (long long)sub * Np) : 0;
+        int jnn = sub + TPP < n ? ld_stream(nb + (long long)(sub + TPP) * Np) : 0;
+        T4 An = A[jn];
+        T4 zan;
+        T2 zbn;
+        if (REUSE && P.noise && sub < n) {
+            zan = ld_stream(zA + (long long)sub * Np + s);
+            zbn = ld_stream(zB + (long long)sub * Np + s);
+        }
+        for (int k = sub; k < n; k += TPP) {
+            const int j = jn;
+            const T4 Aj = An;
+            T4 za;
+            T2 zb;
+            if (REUSE) { za = zan; zb = zbn; }
+            if (k + TPP < n) {
+                jn = jnn;
+                An = A[jn];
+                if (REUSE && P.noise) {
+                    zan = ld_stream(zA + (long long)(k + TPP) * Np + s);
+                    zbn = ld_stream(zB + (long long)(k + TPP) * Np + s);
+                }
+                if (k + 2 * TPP < n) jnn = ld_stream(nb + (long long)(k + 2 * TPP) * Np);
+            }
+            const bool rig = mir_type(Aj) == T_RIGID;
+            const long long at = (long long)k * Np + s;
+            R rx, ry, rz, r2;
+            if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, j, rx, ry, rz, r2)) {
+                if (!REUSE && fl && !rig) {
+                    T4 nm;
+                    nm.x = R(NAN); nm.y = R(0); nm.z = R(0); nm.w = R(0);
+                    st_stream(zA + at, nm);
+                }
+                continue;
+            }
+            const T4 Bj = Bm[j], Cj = Cm[j], Dj = Dm[j];
+            R ox, oy, oz, ce, ex, ey, ez, q, om;
+            Z6<R> z;
+            int zmode = 0;
+            if (REUSE && P.noise && !rig && !isnan(za.x)) {
+                z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
+                zmode = 1;
+            }
+            sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, !rig, zmode, z, ox, oy, oz, ce, ex, ey, ez,
+                         q, om);
+            if (!REUSE && fl && !rig) {
+                T4 zw;
+                zw.x = z.z0; zw.y = z.z1; zw.z = z.z2; zw.w = z.z3;
+                T2 zv;
+                zv.x = z.z4; zv.y = z.z5;
+                st_stream(zA + at, zw);
+                st_stream(zB + at, zv);
+            }
+            R gx, gy, gz, hx, hy, hz;
+            pair_fh(ox, oy, oz, ce, ex, ey, ez, gx, gy, gz, hx, hy, hz);
+            if (rig) {
+                R rcx, rcy, rcz;
+                rxn_of(b, j, rcx, rcy, rcz);
+                const R W = drag_weight(P, q, om);
+                fx = sub_rn(fx, mul_rn(rcx, W));
+                fy = sub_rn(fy, mul_rn(rcy, W));
+                fz = sub_rn(fz, mul_rn(rcz, W));
+            }
+            fx = add_rn(fx, gx);
+            fy = add_rn(fy, gy);
+            fz = add_rn(fz, gz);
+            tx = add_rn(tx, hx);
+            ty = add_rn(ty, hy);
+            tz = add_rn(tz, hz);
+        }
+    }
+    // the TPP lanes of the particle are consecutive: butterfly over them
+#pragma unroll
+    for (int o = 1; o < TPP; o <<= 1) {
+        fx = add_rn(fx, __shfl_xor_sync(0xffffffffu, fx, o));
+        fy = add_rn(fy, __shfl_xor_sync(0xffffffffu, fy, o));
+        fz = add_rn(fz, __shfl_xor_sync(0xffffffffu, fz, o));
+        tx = add_rn(tx, __shfl_xor_sync(0xffffffffu, tx, o));
+        ty = add_rn(ty, __shfl_xor_sync(0xffffffffu, ty, o));
+        tz = add_rn(tz, __shfl_xor_sync(0xffffffffu, tz, o));
+    }
+    if (active && sub == 0) write_fluid_force<R>(b, *Ip, gi, fx, fy, fz, tx, ty, tz, lev);
+}
+
+template <class R, int TPP>
+__global__ void __launch_bounds__(256) k_force_fluid_tpp(Bufs b, int velver)
+{
+    const uint32_t step = (uint32_t)(*b.step);
+    const bool fill = b.use_cache && velver == 1;
+    const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
+                       *b.cache_step == *b.step;
+    __syncthreads();
+    if (fill && blockIdx.x == 0 && threadIdx.x == 0) {
+        *b.cache_epoch = *b.list_epoch;
+        *b.cache_step = *b.step;
+    }
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(b.work, (unsigned long long)(32 / TPP));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= b.N) break;
+        const long long s = (long long)base + lane / TPP;
+        if (reuse) force_fluid_slot_tpp<R, true, TPP>(b, s, lane % TPP, step, false);
+        else force_fluid_slot_tpp<R, false, TPP>(b, s, lane % TPP, step, fill);
+    }
+}
+
 // Newton-3 force pass, phase 1: every fluid or wall particle evaluates the
 // pairs of its owned prefix (see k_neighbors; within h, both non-rigid, at
 // least one fluid) once, stores (f, e x o) in the partner's column of the
@@ -1925,6 +2066,16 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
             k_force_fluid_lean<float, 5><<<persistent_grid(k_force_fluid_lean<float, 5>, 128, b.N), 128, 0, st>>>(b, velver);
         else
             k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b, velver);
+    } else if (b.tpp == 2 || b.tpp == 4) {
+        // the direct pass with several lanes per particle: N x tpp threads
+        const long long nt = b.N * (long long)b.tpp;
+        if (precision == SDPD_PREC_SPLIT) {
+            if (b.tpp == 2) k_force_fluid_tpp<float, 2><<<persistent_grid(k_force_fluid_tpp<float, 2>, bs, nt), bs, 0, st>>>(b, velver);
+            else k_force_fluid_tpp<float, 4><<<persistent_grid(k_force_fluid_tpp<float, 4>, bs, nt), bs, 0, st>>>(b, velver);
+        } else {
+            if (b.tpp == 2) k_force_fluid_tpp<double, 2><<<persistent_grid(k_force_fluid_tpp<double, 2>, bs, nt), bs, 0, st>>>(b, velver);
+            else k_force_fluid_tpp<double, 4><<<persistent_grid(k_force_fluid_tpp<double, 4>, bs, nt), bs, 0, st>>>(b, velver);
+        }
     } else if (precision == SDPD_PREC_SPLIT) {
         k_force_fluid<float><<<persistent_grid(k_force_fluid<float>, bs, b.N), bs, 0, st>>>(b, velver);
     } else {

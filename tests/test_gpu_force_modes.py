@@ -90,3 +90,30 @@ def test_variants_match_oracle(precision, mode):
     assert rel_l2(g["F"], o["F"]) < TOL_FORCE[precision]
     check_per_type(g, o, case["type"], TOL_FORCE[precision])
     sim.close()
+
+
+@pytest.mark.parametrize("tpp", [2, 4])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_lanes_per_particle_sum_order_only(precision, tpp):
+    # several lanes per particle change the summation order of the direct
+    # pass and nothing else; the same on every run
+    made = CASES["dambreak_small"]()
+    insts = [_moving(made, 3)]
+
+    def run():
+        sim = B.Sim(insts, precision=precision)
+        sim.set_force_mode(0)
+        sim.set_threads_per_particle(tpp)
+        sim.step_count = 4
+        sim.step(2)
+        out = sim.state(0, density=False)
+        sim.check()
+        sim.close()
+        return out
+
+    ref = _run(insts, precision, 0, True, steps=2)[0]
+    a, b = run(), run()
+    for q in ("x", "v", "w", "F", "N"):
+        assert np.array_equal(a[q], b[q]), q
+    tol = 1e-12 if precision == B.SDPD_PREC_FP64 else 1e-5
+    assert rel_l2(a["F"], ref["F"]) < tol and rel_l2(a["N"], ref["N"]) < tol
