@@ -7,7 +7,7 @@
 //   K3 scatter into cell ranges, K4 rank by gid inside each cell (deterministic
 //      order, so every later sum is reproducible bit for bit)
 //   K5 gather of the cell-sorted mirrors (float4 / double4 records)
-//   K6 per particle, the ascending list of neighbours j != i within the build
+//   K6 per particle, the list of neighbours j != i within the build
 //      radius rb = h (1 + skin) from the surrounding cells
 //   K7 reverse index of the Newton-3 force pass
 // The list is a superset of the pairs within h; every consumer re-decides
@@ -206,9 +206,10 @@ __global__ void k_gather(Bufs b, int precision, const int *gate)
 // Newton-3 ownership, balanced so that every particle owns about half of its
 // pairs whatever its position in the cell: the pair of instance-local slots
 // a < b belongs to a when bit 15 of the hash (a * 0x9E3779B1) ^
-// (b * 0x85EBCA77) is set, else to b.  The list is written as [owned][not owned], each part ascending in
-// slot (cells visited in ascending key), so the owned pairs are the prefix
-// [0, nfirst) and a partner's position is found by binary search in it.
+// (b * 0x85EBCA77) is set, else to b.  The list is written as [owned][not
+// owned], the owned part ascending in slot (cells visited in ascending key),
+// the other descending, so the owned pairs are the prefix [0, nfirst) and a
+// partner's position is found by binary search in it.
 __device__ __forceinline__ bool pair_owned(long long s, int j, int base)
 {
     // instance-local slots: an instance owns the same pairs alone or batched
@@ -219,10 +220,13 @@ __device__ __forceinline__ bool pair_owned(long long s, int j, int base)
 }
 
 
+// The candidate test of a pair (i, j) with j's record Aj and the offset
+// (sx, sy, sz) of j's cell: within rb (float), or both rigid and within
+// contact range (flagged NB_FAR).
 __device__ __forceinline__ bool nb_test(const Bufs &b, const Inst &I, const float4 &Ai, int ti, float Ri,
-                                        int j, float sx, float sy, float sz, uint32_t &entry, int &tj)
+                                        int j, const float4 &Aj, float sx, float sy, float sz, uint32_t &entry,
+                                        int &tj)
 {
-    const float4 Aj = b.A32[j];
     tj = unpack_type(__float_as_uint(Aj.w));
     const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy, dz = (Ai.z - Aj.z) - sz;
     const float r2f = dx * dx + dy * dy + dz * dz;
@@ -236,68 +240,93 @@ __device__ __forceinline__ bool nb_test(const Bufs &b, const Inst &I, const floa
     return false;
 }
 
-__global__ void k_neighbors(Bufs b, const int *gate)
+// One warp per cell, its particles 32 at a time: all lanes share the cell's
+// 27 neighbour cells, so the candidates' records are read once per warp --
+// 32 consecutive records, coalesced, into shared memory -- and every lane
+// tests them from there (broadcast reads) instead of each lane loading every
+// candidate from global memory.  Cells and candidates are visited in
+// ascending order, as a per-particle scan would.
+constexpr int NB_WARPS = 8;
+
+__global__ void __launch_bounds__(NB_WARPS * 32) k_neighbors(Bufs b, const int *gate)
 {
     GATE;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= b.N) return;
-    const int gi = b.perm[s];
-    const Inst &I = b.inst[b.pinst[gi]];
-    const int ti = b.stype[s];
-    const float Ri = (ti == T_RIGID) ? (float)b.R[gi] : 0.f;
-    const float4 Ai = b.A32[s];
-    const int *adj = b.cell_adj + (long long)b.skey[s] * 27;
-    const int base = b.cstart[I.cell_base];  // first slot of the instance
+    __shared__ float4 stage[NB_WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * NB_WARPS + w;
+    if (c >= b.ncell_total) return;   // the whole warp
+    const int s0 = b.cstart[c], s1 = b.cstart[c + 1];
+    if (s0 == s1) return;
+    const int *adj = b.cell_adj + (long long)c * 27;
+    const Inst &I = b.inst[b.pinst[b.perm[s0]]];   // a cell belongs to one instance
+    const int base = b.cstart[I.cell_base];           // first slot of the instance
     const long long Np = b.Npad;
-    int *col = b.nbr + s;                     // this particle's column, entry k at col[k * Np]
     const int cap = b.cap;
-    // one scan in ascending slot order: owned pairs from the front, the
-    // others from the back of the column (so in descending positions)
-    int nf = 0, m = 0;
-    bool rig = false;
-    uint32_t entry;
-    int tj;
-    for (int q = 0; q < 27; ++q) {
-        const int code = adj[q];
-        if (code < 0) break;
-        const int key = code >> 5, oc = code & 31;
-        const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
-                    sz = (float)(oc / 9 - 1) * I.csf[2];
-        const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
-        for (int j = j0; j < j1; ++j) {
-            if (j == s || !nb_test(b, I, Ai, ti, Ri, j, sx, sy, sz, entry, tj)) continue;
-            rig |= (tj == T_RIGID);
-            if (pair_owned(s, j, base)) {
-                if (nf + m < cap) col[(long long)nf * Np] = (int)entry;
-                ++nf;
-            } else {
-                if (nf + m < cap) col[(long long)(cap - 1 - m) * Np] = (int)entry;
-                ++m;
+    for (int chunk = s0; chunk < s1; chunk += 32) {
+        const int s = chunk + lane;
+        const bool act = s < s1;
+        int ti = T_FLUID;
+        float Ri = 0.f;
+        float4 Ai = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+            ti = b.stype[s];
+            Ri = (ti == T_RIGID) ? (float)b.R[b.perm[s]] : 0.f;
+            Ai = b.A32[s];
+        }
+        int *col = b.nbr + s;   // this particle's column, entry k at col[k * Np]
+        // one scan in ascending slot order: owned pairs from the front, the
+        // others from the back of the column (so in descending positions)
+        int nf = 0, m = 0;
+        bool rig = false;
+        for (int q = 0; q < 27; ++q) {
+            const int code = adj[q];
+            if (code < 0) break;
+            const int key = code >> 5, oc = code & 31;
+            const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
+                        sz = (float)(oc / 9 - 1) * I.csf[2];
+            const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
+            for (int jb = j0; jb < j1; jb += 32) {
+                const int jj = jb + lane;
+                __syncwarp();
+                stage[w][lane] = jj < j1 ? b.A32[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                if (!act) continue;
+                const int cnt = min(32, j1 - jb);
+                for (int t = 0; t < cnt; ++t) {
+                    const int j = jb + t;
+                    uint32_t entry;
+                    int tj;
+                    if (j == s || !nb_test(b, I, Ai, ti, Ri, j, stage[w][t], sx, sy, sz, entry, tj)) continue;
+                    rig |= (tj == T_RIGID);
+                    if (pair_owned(s, j, base)) {
+                        if (nf + m < cap) col[(long long)nf * Np] = (int)entry;
+                        ++nf;
+                    } else {
+                        if (nf + m < cap) col[(long long)(cap - 1 - m) * Np] = (int)entry;
+                        ++m;
+                    }
+                }
             }
         }
-    }
-    const int n = nf + m;
-    // the pair buffer holds capown rows of owned and of non-owned entries
-    if (nf > b.capown || m > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
-    if (n > cap) {
-        atomicOr(b.err, ERR_NBR_CAP);
-    } else {
-        // the back region [cap - m, cap) holds the non-owned entries in
-        // descending order: reverse it in place, then move it down to
-        // [nf, n) in ascending order (destination below the source, so an
-        // ascending copy never overwrites an entry still to be read)
-        for (int k = 0; k < m / 2; ++k) {
-            const long long a = (long long)(cap - m + k) * Np, c = (long long)(cap - 1 - k) * Np;
-            const int t = col[a];
-            col[a] = col[c];
-            col[c] = t;
+        if (!act) continue;
+        const int n = nf + m;
+        // the pair buffer holds capown rows of owned and of non-owned entries
+        if (nf > b.capown || m > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+        if (n > cap) {
+            atomicOr(b.err, ERR_NBR_CAP);
+        } else {
+            // the back region [cap - m, cap) holds the non-owned entries in
+            // descending slot order: move it down to [nf, n) as it is
+            // (destination below the source, so an ascending copy never
+            // overwrites an entry still to be read); only the owned prefix
+            // needs ascending order (the reverse index searches it)
+            if (nf < cap - m)
+                for (int k = 0; k < m; ++k) col[(long long)(nf + k) * Np] = col[(long long)(cap - m + k) * Np];
         }
-        if (nf < cap - m)
-            for (int k = 0; k < m; ++k) col[(long long)(nf + k) * Np] = col[(long long)(cap - m + k) * Np];
+        b.nfirst[s] = min(nf, min(cap, b.capown));
+        b.ncnt[s] = min(n, cap);
+        b.nbflag[s] = rig ? 1 : 0;
     }
-    b.nfirst[s] = min(nf, min(cap, b.capown));
-    b.ncnt[s] = min(n, cap);
-    b.nbflag[s] = rig ? 1 : 0;
 }
 
 // For every non-owned entry k of s (positions [nfirst, n)), the position r
@@ -382,7 +411,7 @@ void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, c
         k_scatter<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
         k_rank<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
         k_gather<<<nblk(b.N, 256), 256, 0, st>>>(b, precision, gate);
-        k_neighbors<<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
+        k_neighbors<<<nblk(nc, NB_WARPS), NB_WARPS * 32, 0, st>>>(b, gate);
         if (need_rev) k_rev<<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
     }
     k_build_done<<<1, 1, 0, st>>>(b, gate);
