@@ -8,9 +8,19 @@ The arithmetic lives in ``sdpd_oracle.c`` (Algorithms 1 and 2 and the
 equations of Section 2 of the paper, in their order); this module compiles it
 with gcc (``-O2 -ffp-contract=off``) on first use and marshals numpy arrays.
 
-Parity pins: see tests/test_oracle_*.py.  Absolute values of the
-viscometer-with-solids and dam-break trajectories are parity unpinned (the
-paper prints no data for them); only invariants are checked there.
+Parity pins (tests/test_oracle_*.py): every function here is checked
+against something other than itself -- closed forms (Lucy kernel integral,
+perfect-lattice density, drag laws, Reynolds lubrication, Archimedes'
+buoyancy, the viscous part of the pressure-gradient force on a moving
+sphere, restitution and rolling of DEM contacts, free fall, the Poiseuille
+profile and its read-outs), brute force (neighbour sets), invariants
+(antisymmetry, momentum, dissipation, fluctuation-dissipation, equipartition)
+and published known-answer vectors (Philox4x32-10).  Parity unpinned, at the
+level of whole trajectories only: the absolute viscosity of the viscometer
+with solids and the dam-break run (the paper prints no data for them), and
+the settling velocity of the sedimentation case (its ODE does not hold for
+the model as printed); their forces are pinned one by one, and only
+invariants are checked for the runs.
 """
 from __future__ import annotations
 
