@@ -513,12 +513,15 @@ def ncu_counters(name="counters_sedimentation"):
 
 
 def pipe_util(c, fp64):
+    """Pipe utilisation of a profiled kernel (fractions), from whatever the
+    counters file holds for it; None without a capture."""
     if not c:
         return None
-    if fp64:
-        return {"fp64_pipe": c["fp64_pipe_pct"] / 100.0, "lanes_active": c["threads_per_inst"] / 32.0}
-    return {"fma_pipe": c["fma_pipe_pct"] / 100.0, "alu_pipe": c["alu_pipe_pct"] / 100.0,
-            "issue_active": c["issue_active_pct"] / 100.0, "lanes_active": c["threads_per_inst"] / 32.0}
+    keys = ({"fp64_pipe": "fp64_pipe_pct", "lanes_active": "threads_per_inst"} if fp64 else
+            {"fma_pipe": "fma_pipe_pct", "alu_pipe": "alu_pipe_pct", "issue_active": "issue_active_pct",
+             "lanes_active": "threads_per_inst"})
+    out = {k: c[v] / (32.0 if v == "threads_per_inst" else 100.0) for k, v in keys.items() if v in c}
+    return out or None
 
 
 def measured_peaks():
