@@ -256,6 +256,17 @@ sdpd_status sdpd_set_block_size(sdpd_ctx *ctx, int threads);
  * Invalidates the current graph.  Synchronous. */
 sdpd_status sdpd_set_threads_per_particle(sdpd_ctx *ctx, int tpp);
 
+/* Cells of the neighbour search per minimum cell width (Algorithm 1, Section
+ * 3.2, the background grid): 1 (default) or 2.  The minimum width is
+ * max(h (1 + skin), largest sphere diameter + skin h); with 2 the cells are
+ * half as wide, the stencil reaches 2 cells each way (125 cells, about 0.58
+ * of the 27-cell volume) and the lists are built with one lane per candidate
+ * instead of one per particle.  The listed pairs are the same (every pass
+ * re-decides r_ij < h exactly); particles are ordered by the finer cells,
+ * so results differ only by summation order.  A tuning knob.  Invalidates
+ * the grid and the graph.  Synchronous.  SDPD_E_INVALID for any other value. */
+sdpd_status sdpd_set_cell_factor(sdpd_ctx *ctx, int cells);
+
 /* Verlet skin as a fraction of h (default 0.03): neighbour lists hold the
  * pairs within h (1 + skin) and are reused by later evaluations until some
  * particle has moved skin h / 2 since the build (decided on the device each

@@ -3,8 +3,8 @@
 For one workload (a list of instances and a precision) it times full steps
 under each candidate setting -- force-pass variant (Newton-3 half pairs,
 direct, or the pair stream through shared memory at two register caps),
-Verlet skin, pair-kernel block size, lanes per particle of the direct pass
--- picks the fastest, and keeps
+Verlet skin, pair-kernel block size, lanes per particle of the direct pass,
+full- or half-size cells of the neighbour search -- picks the fastest, and keeps
 the choice in a JSON file keyed by GPU name, precision and size class (total
 particles rounded to a power of two, number of instances), so later contexts
 of the same class reuse it without measuring again.
@@ -34,6 +34,7 @@ CANDIDATES = {
     "skin": (0.0, 0.03, 0.06, 0.12),
     "block": (64, 128, 256),
     "tpp": (1, 2, 4),   # lanes per particle of the direct pass
+    "cells": (1, 2),    # cells per minimum cell width of the neighbour search
 }
 
 
@@ -66,14 +67,22 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
 
 
 def _sampled(setting, candidates, precision):
-    """Settings measured: the Newton-3 passes over the whole grid (the push
-    variant for FP32 pairs only); the direct pass at the default block (every
-    skin) and without skin (every block), its lean form (FP32 only, 128
-    threads) at the three smaller skins; the pair stream, when asked for,
-    at the two larger blocks and the two middle skins, the three-block
-    variant for FP32 pairs only."""
+    """Settings measured, with full-size cells: the Newton-3 passes over the
+    whole grid (the push variant for FP32 pairs only); the direct pass at the
+    default block (every skin) and without skin (every block), its lean form
+    (FP32 only, 128 threads) at the three smaller skins; the pair stream,
+    when asked for, at the two larger blocks and the two middle skins, the
+    three-block variant for FP32 pairs only.  Half-size cells: the Newton-3,
+    direct and lean direct passes at the default block and the three smaller
+    skins."""
     mode, skin, block = setting["newton3"], setting["skin"], setting["block"]
     skins = candidates["skin"]
+    if setting.get("cells", 1) != 1:
+        # half-size cells: one lane per particle, the default block, the
+        # three smaller skins; Newton 3, direct and lean direct (FP32)
+        if setting.get("tpp", 1) != 1 or block != 128 or skin not in skins[:3]:
+            return False
+        return mode in (0, 1) or (mode == 5 and precision != B.SDPD_PREC_FP64)
     if setting.get("tpp", 1) != 1:
         # several lanes per particle: the direct pass at the default block
         # and the default skin
@@ -113,6 +122,7 @@ def apply(sim: "B.Sim", setting: dict) -> None:
     sim.set_force_mode(int(setting["newton3"]))
     sim.set_threads_per_particle(int(setting.get("tpp", 1)))
     sim.set_skin(float(setting["skin"]))
+    sim.set_cell_factor(int(setting.get("cells", 1)))
     sim.set_block_size(int(setting["block"]))
 
 

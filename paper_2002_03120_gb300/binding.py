@@ -74,7 +74,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_compute_density", "sdpd_couple_drag", "sdpd_compute_forces", "sdpd_integrate",
            "sdpd_step", "sdpd_viscosity_probe", "sdpd_get_state", "sdpd_get_drag",
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
-           "sdpd_set_force_mode", "sdpd_set_noise_cache", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_set_threads_per_particle", "sdpd_density_noalloc",
+           "sdpd_set_force_mode", "sdpd_set_noise_cache", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_set_threads_per_particle", "sdpd_set_cell_factor", "sdpd_density_noalloc",
            "sdpd_check",
            "sdpd_last_error", "sdpd_noise_normals", "sdpd_philox4x32_10", "sdpd_alu_peaks", "sdpd_viscosity_fit", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
            "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
@@ -134,6 +134,7 @@ def load(build_if_missing: bool = True):
         "sdpd_noise_normals": (st, [C.c_int, C.c_ulonglong, C.c_int, C.c_uint, C.c_longlong, vp, vp, vp]),
         "sdpd_philox4x32_10": (st, [C.c_longlong, vp, vp, vp]),
         "sdpd_set_threads_per_particle": (st, [vp, C.c_int]),
+        "sdpd_set_cell_factor": (st, [vp, C.c_int]),
         "sdpd_alu_peaks": (st, [vp]),
         "mlp_init": (st, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.POINTER(vp)]),
         "mlp_destroy": (None, [vp]),
@@ -383,6 +384,10 @@ class Sim:
 
     def set_threads_per_particle(self, tpp: int):
         _check(load().sdpd_set_threads_per_particle(self._h, int(tpp)))
+
+    def set_cell_factor(self, cells: int):
+        """Cells per minimum cell width of the neighbour search: 1 or 2."""
+        _check(load().sdpd_set_cell_factor(self._h, int(cells)))
 
     def set_skin(self, skin: float):
         _check(load().sdpd_set_skin(self._h, float(skin)))

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -58,6 +59,7 @@ struct sdpd_ctx {
                                        // fewer registers (FP32)
     int noise_cache = 1;               // second evaluation of a step reuses the first one's normals
     double skin = 0.03;                // Verlet skin as a fraction of h
+    int cell_sub = 1;                  // cells per minimum cell width: 1 (27-cell stencil) or 2 (125)
     bool geometry_ready = false, cells_valid = false, density_valid = false, drag_valid = false;
     int sticky_err = 0;
     long long host_step = 0;
@@ -171,14 +173,21 @@ sdpd_status prepare(sdpd_ctx *c)
                 skin = std::min(skin, std::max(0.0, room * 0.999));
             }
         const double rb = p.r_c * (1.0 + skin);
+        // cmin bounds the reach of any listed pair; cells are cmin / sub wide
+        // and the stencil reaches sub cells each way
         const double cmin = std::max(rb, 2.0 * H.Rmax + skin * p.r_c);
+        const int sub = c->cell_sub;
+        const double cw = cmin / sub;
+        I.sub = sub;
         for (int a = 0; a < 3; ++a) {
             I.origin[a] = p.origin[a];
             I.box[a] = p.box[a];
             I.periodic[a] = p.periodic[a] ? 1 : 0;
             if (p.periodic[a]) {
-                int nc = (int)std::floor(p.box[a] / cmin);
-                if (nc < 3) {
+                // 3 cells of cmin fit, so at least 2 sub + 1 cells of cw do:
+                // the stencil never meets the same cell twice
+                int nc = (int)std::floor(p.box[a] / cw);
+                if (nc < 3 || (int)std::floor(p.box[a] / cmin) < 3) {
                     char buf[160];
                     std::snprintf(buf, sizeof buf,
                                   "instance %d axis %d: periodic box must hold 3 cells of max(h, 2 R_max)", k, a);
@@ -190,9 +199,9 @@ sdpd_status prepare(sdpd_ctx *c)
             } else {
                 const double lo = std::min(H.xmin[a], p.origin[a]) - 0.5 * cmin;
                 const double hi = std::max(H.xmax[a], p.origin[a] + p.box[a]) + 0.5 * cmin;
-                I.cs[a] = cmin;
+                I.cs[a] = cw;
                 I.lo[a] = lo;
-                I.nc[a] = (int)std::ceil((hi - lo) / cmin);
+                I.nc[a] = (int)std::ceil((hi - lo) / cw);
             }
             if (I.nc[a] > 1023) return fail(SDPD_E_INVALID, "more than 1023 cells on an axis");
             I.inv_cs[a] = 1.0 / I.cs[a];
@@ -273,42 +282,58 @@ sdpd_status prepare(sdpd_ctx *c)
     }
     Bufs &b = c->b;
     b.ncell_total = cell_base;
+    b.cell_sub = c->cell_sub;
     int *rank_d = nullptr;
     ALLOC(rank_d, cell_base, true);
     CUDA_TRY(cudaMemcpy(rank_d, rank_all.data(), sizeof(int) * cell_base, cudaMemcpyHostToDevice));
     b.cell_rank = rank_d;
-    // neighbour cells of every cell, ascending key, with the offset code
-    // (ox+1) + 3 (oy+1) + 9 (oz+1): neighbour lists then come out sorted by slot
+    // neighbour cells of every cell (offsets -sub..sub per axis), ascending
+    // key, with the offset code (ox+2) + 5 (oy+2) + 25 (oz+2): neighbour
+    // lists then come out sorted by slot.  Cells are split over host threads.
     {
-        std::vector<int> adj((size_t)cell_base * 27, -1);
-        for (int k = 0; k < c->n_inst; ++k) {
-            const Inst &I = c->inst[k];
-            for (int z = 0; z < I.nc[2]; ++z)
-                for (int y = 0; y < I.nc[1]; ++y)
-                    for (int x = 0; x < I.nc[0]; ++x) {
-                        const int lin = (z * I.nc[1] + y) * I.nc[0] + x;
-                        const int key = I.cell_base + rank_all[I.cell_base + lin];
-                        std::vector<std::pair<int, int>> nbs;
-                        for (int oz = -1; oz <= 1; ++oz)
-                            for (int oy = -1; oy <= 1; ++oy)
-                                for (int ox = -1; ox <= 1; ++ox) {
-                                    int cc[3] = { x + ox, y + oy, z + oz };
-                                    bool ok = true;
-                                    for (int a = 0; a < 3; ++a) {
-                                        if (I.periodic[a]) cc[a] = (cc[a] + I.nc[a]) % I.nc[a];
-                                        else if (cc[a] < 0 || cc[a] >= I.nc[a]) ok = false;
-                                    }
-                                    if (!ok) continue;
-                                    const int l2 = (cc[2] * I.nc[1] + cc[1]) * I.nc[0] + cc[0];
-                                    const int k2 = I.cell_base + rank_all[I.cell_base + l2];
-                                    nbs.push_back({ k2, (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1) });
-                                }
-                        std::sort(nbs.begin(), nbs.end());
-                        for (size_t q = 0; q < nbs.size(); ++q)
-                            adj[(size_t)key * 27 + q] = (nbs[q].first << 5) | nbs[q].second;
-                    }
+        if (cell_base >= (1 << 24)) return fail(SDPD_E_INVALID, "too many cells");
+        std::vector<int> adj((size_t)cell_base * ADJ, -1);
+        std::vector<int> inst_of(cell_base);
+        for (int k = 0; k < c->n_inst; ++k)
+            std::fill(inst_of.begin() + c->inst[k].cell_base,
+                      inst_of.begin() + c->inst[k].cell_base + c->inst[k].ncell, k);
+        auto fill = [&](int lin0, int lin1) {
+            std::pair<int, int> nbs[ADJ];
+            for (int gl = lin0; gl < lin1; ++gl) {
+                const Inst &I = c->inst[inst_of[gl]];
+                const int lin = gl - I.cell_base, d = I.sub;
+                const int x = lin % I.nc[0], y = (lin / I.nc[0]) % I.nc[1], z = lin / (I.nc[0] * I.nc[1]);
+                const int key = I.cell_base + rank_all[gl];
+                int nn = 0;
+                for (int oz = -d; oz <= d; ++oz)
+                    for (int oy = -d; oy <= d; ++oy)
+                        for (int ox = -d; ox <= d; ++ox) {
+                            int cc[3] = { x + ox, y + oy, z + oz };
+                            bool ok = true;
+                            for (int a = 0; a < 3; ++a) {
+                                if (I.periodic[a]) cc[a] = (cc[a] + I.nc[a]) % I.nc[a];
+                                else if (cc[a] < 0 || cc[a] >= I.nc[a]) ok = false;
+                            }
+                            if (!ok) continue;
+                            const int l2 = (cc[2] * I.nc[1] + cc[1]) * I.nc[0] + cc[0];
+                            const int k2 = I.cell_base + rank_all[I.cell_base + l2];
+                            nbs[nn++] = { k2, (ox + 2) + 5 * (oy + 2) + 25 * (oz + 2) };
+                        }
+                std::sort(nbs, nbs + nn);
+                for (int q = 0; q < nn; ++q) adj[(size_t)key * ADJ + q] = (nbs[q].first << 7) | nbs[q].second;
+            }
+        };
+        const int nth = std::max(1, std::min((int)std::thread::hardware_concurrency(),
+                                             std::min(16, cell_base / 4096 + 1)));
+        if (nth == 1) {
+            fill(0, cell_base);
+        } else {
+            std::vector<std::thread> pool;
+            for (int t = 0; t < nth; ++t)
+                pool.emplace_back(fill, (int)((long long)cell_base * t / nth),
+                                  (int)((long long)cell_base * (t + 1) / nth));
+            for (auto &th : pool) th.join();
         }
-        if (cell_base >= (1 << 26)) return fail(SDPD_E_INVALID, "too many cells");
         int *adj_d = nullptr;
         ALLOC(adj_d, adj.size(), true);
         CUDA_TRY(cudaMemcpy(adj_d, adj.data(), sizeof(int) * adj.size(), cudaMemcpyHostToDevice));
@@ -425,6 +450,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
         return fail(SDPD_E_CUDA, "no CUDA device");
     init_pair_kernels();   // kernel attributes, set outside any stream capture
+    init_cell_kernels();
     sdpd_ctx *c = new sdpd_ctx();
     c->n_inst = n_instances;
     c->precision = precision;
@@ -452,6 +478,7 @@ sdpd_status sdpd_init(const sdpd_params *params, int n_instances, const long lon
     b.K = c->K;
     b.pair_block = 128;
     b.tpp = 1;
+    b.cell_sub = 1;
     auto cleanup = [&](sdpd_status s) {
         sdpd_destroy(c);
         return s;
@@ -930,6 +957,20 @@ sdpd_status sdpd_set_threads_per_particle(sdpd_ctx *c, int tpp)
     if (tpp != c->b.tpp) {
         c->b.tpp = tpp;
         drop_graph(c);
+    }
+    return SDPD_OK;
+}
+
+sdpd_status sdpd_set_cell_factor(sdpd_ctx *c, int sub)
+{
+    if (!c) return fail(SDPD_E_INVALID, "NULL context");
+    if (sub != 1 && sub != 2) return fail(SDPD_E_INVALID, "cells per minimum width must be 1 or 2");
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (sub != c->cell_sub) {
+        c->cell_sub = sub;
+        c->geometry_ready = false;
+        drop_graph(c);
+        c->cells_valid = c->density_valid = c->drag_valid = false;
     }
     return SDPD_OK;
 }

@@ -27,12 +27,17 @@ constexpr int ERR_NBR_CAP = 1, ERR_CELL_CAP = 2, ERR_CONTACT_CAP = 4, ERR_NONFIN
 
 // rigid-pair list entries beyond h (contact only) carry this flag
 constexpr uint32_t NB_FAR = 0x80000000u;
+
+// neighbour-cell table: up to 5 x 5 x 5 cells per cell (half-size cells),
+// entries (key << 7) | ((ox + 2) + 5 (oy + 2) + 25 (oz + 2)), -1 = none
+constexpr int ADJ = 125;
 constexpr int PLANE_BASE = -16;   // contact-history partner codes of wall planes
 
 // Per-instance constants, derived on the host from sdpd_params.
 struct Inst {
     double origin[3], box[3], lo[3], cs[3], inv_cs[3];
     int nc[3], periodic[3];
+    int sub;                   // cells per minimum cell width (1 or 2): the stencil reaches +-sub cells
     int cell_base, ncell;
     long long p_begin, p_end;
     double dx, rc, rc2, inv_rc, dt, hdt, isqrt_dt;
@@ -70,6 +75,7 @@ struct Bufs {
     int n_inst, ncell_total, nrigid, cap, K;
     int pair_block;            // threads per block of the pair kernels (64, 128 or 256)
     int tpp;                   // lanes per particle of the direct force pass (1, 2 or 4)
+    int cell_sub;              // cells per minimum cell width (1 or 2): picks the list kernel
     const Inst *inst;          // [n_inst]
     // master state (gid order)
     double *x, *v, *w, *F, *T;
@@ -79,7 +85,7 @@ struct Bufs {
     int *rigid_gid;            // rigid index -> gid
     // cells
     const int *cell_rank;      // [ncell_total] linear cell -> Morton rank (within instance)
-    const int *cell_adj;       // [ncell_total][27] (key << 5 | offset code), ascending key, -1 = none
+    const int *cell_adj;       // [ncell_total][ADJ] (key << 7 | offset code), ascending key, -1 = none
     int *key, *slot_in_cell, *ccount, *cstart, *tmp_perm, *perm, *slot_of;
     int *scan_partials;        // [ceil(ncell_total/1024)+1]
     // mirrors
@@ -286,22 +292,25 @@ __device__ __forceinline__ void pair_normals(uint32_t gi, uint32_t gj, uint32_t 
 template <class R> struct Geo;
 template <> struct Geo<float> {
     bool p0, p1, p2;
-    int n0, n1, n2;
+    int n0, n1, n2, dm;   // dm: the farthest neighbour cell of the stencil (1 or 2)
     float c0, c1, c2;
     float glo, ghi;   // r^2 guard band (copied: a store in a pair loop may not
                       // force them to be reloaded from the instance table)
     __device__ __forceinline__ explicit Geo(const Inst &I)
         : p0(I.periodic[0]), p1(I.periodic[1]), p2(I.periodic[2]), n0(I.nc[0]), n1(I.nc[1]),
-          n2(I.nc[2]), c0(I.csf[0]), c1(I.csf[1]), c2(I.csf[2]), glo(I.guard_lo), ghi(I.guard_hi) {}
+          n2(I.nc[2]), dm(I.sub), c0(I.csf[0]), c1(I.csf[1]), c2(I.csf[2]), glo(I.guard_lo),
+          ghi(I.guard_hi) {}
     __device__ __forceinline__ void disp(const float4 &Ai, const float4 &Aj, float &rx, float &ry,
                                          float &rz) const
     {
         const uint32_t bi = __float_as_uint(Ai.w), bj = __float_as_uint(Aj.w);
         int d0 = unpack_cx(bi) - unpack_cx(bj), d1 = unpack_cy(bi) - unpack_cy(bj),
             d2 = unpack_cz(bi) - unpack_cz(bj);
-        if (p0) d0 = d0 > 1 ? d0 - n0 : (d0 < -1 ? d0 + n0 : d0);
-        if (p1) d1 = d1 > 1 ? d1 - n1 : (d1 < -1 ? d1 + n1 : d1);
-        if (p2) d2 = d2 > 1 ? d2 - n2 : (d2 < -1 ? d2 + n2 : d2);
+        // neighbours are at most dm cells apart and periodic axes hold at
+        // least 2 dm + 1 cells, so a larger difference is a wrap
+        if (p0) d0 = d0 > dm ? d0 - n0 : (d0 < -dm ? d0 + n0 : d0);
+        if (p1) d1 = d1 > dm ? d1 - n1 : (d1 < -dm ? d1 + n1 : d1);
+        if (p2) d2 = d2 > dm ? d2 - n2 : (d2 < -dm ? d2 + n2 : d2);
         rx = (Ai.x - Aj.x) + (float)d0 * c0;
         ry = (Ai.y - Aj.y) + (float)d1 * c1;
         rz = (Ai.z - Aj.z) + (float)d2 * c2;
@@ -388,6 +397,7 @@ void launch_drag(const Bufs &b, int precision, cudaStream_t st);
 // force mode: 0 direct, 1 Newton 3 (half pairs + gather), 2 pair stream
 void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaStream_t st);
 void init_pair_kernels();
+void init_cell_kernels();
 void launch_mark_pairs(const Bufs &b, uint8_t *flags, cudaStream_t st);
 void launch_integrate(const Bufs &b, int precision, int velver, int any_artvis, cudaStream_t st);
 void launch_step_done(const Bufs &b, cudaStream_t st);

@@ -15,6 +15,8 @@
 // stays valid while no particle has moved more than skin h / 2 since the
 // build; the drift raises `need_build` when one has, and every kernel here
 // is gated on that flag inside the captured step.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sdpd {
@@ -198,8 +200,9 @@ __global__ void k_gather(Bufs b, int precision, const int *gate)
 }
 
 // Neighbour list of particle (slot) s: candidates from the cells around s's
-// cell (cells are at least max(rb, largest sphere diameter + skin) wide,
-// periodic axes at least 3 cells).  A pair is listed when r < rb (float test:
+// cell (cells are at least max(rb, largest sphere diameter + skin) / sub
+// wide and the stencil reaches sub cells each way, sub = 1 or 2; periodic
+// axes at least 2 sub + 1 cells).  A pair is listed when r < rb (float test:
 // the list only has to be a superset of the pairs within h), or when both are
 // rigid and r < R_i + R_j + skin h (contact range; flagged NB_FAR).
 //
@@ -241,23 +244,18 @@ __device__ __forceinline__ bool nb_test(const Bufs &b, const Inst &I, const floa
 }
 
 // One warp per cell, its particles 32 at a time: all lanes share the cell's
-// 27 neighbour cells, so the candidates' records are read once per warp --
+// neighbour cells (27, or 125 with half-size cells), so the candidates' records are read once per warp --
 // 32 consecutive records, coalesced, into shared memory -- and every lane
 // tests them from there (broadcast reads) instead of each lane loading every
 // candidate from global memory.  Cells and candidates are visited in
 // ascending order, as a per-particle scan would.
 constexpr int NB_WARPS = 8;
 
-__global__ void __launch_bounds__(NB_WARPS * 32) k_neighbors(Bufs b, const int *gate)
+// The lists of cell c's particles [s0, s1), one lane per particle; stage:
+// 32 float4 of this warp's shared memory.
+__device__ void nb_scan_cell(const Bufs &b, int c, int s0, int s1, float4 *stage, int lane)
 {
-    GATE;
-    __shared__ float4 stage[NB_WARPS][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * NB_WARPS + w;
-    if (c >= b.ncell_total) return;   // the whole warp
-    const int s0 = b.cstart[c], s1 = b.cstart[c + 1];
-    if (s0 == s1) return;
-    const int *adj = b.cell_adj + (long long)c * 27;
+    const int *adj = b.cell_adj + (long long)c * ADJ;
     const Inst &I = b.inst[b.pinst[b.perm[s0]]];   // a cell belongs to one instance
     const int base = b.cstart[I.cell_base];           // first slot of the instance
     const long long Np = b.Npad;
@@ -278,17 +276,17 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbors(Bufs b, const int *
         // others from the back of the column (so in descending positions)
         int nf = 0, m = 0;
         bool rig = false;
-        for (int q = 0; q < 27; ++q) {
+        for (int q = 0; q < ADJ; ++q) {
             const int code = adj[q];
             if (code < 0) break;
-            const int key = code >> 5, oc = code & 31;
-            const float sx = (float)(oc % 3 - 1) * I.csf[0], sy = (float)((oc / 3) % 3 - 1) * I.csf[1],
-                        sz = (float)(oc / 9 - 1) * I.csf[2];
+            const int key = code >> 7, oc = code & 127;
+            const float sx = (float)(oc % 5 - 2) * I.csf[0], sy = (float)((oc / 5) % 5 - 2) * I.csf[1],
+                        sz = (float)(oc / 25 - 2) * I.csf[2];
             const int j0 = b.cstart[key], j1 = b.cstart[key + 1];
             for (int jb = j0; jb < j1; jb += 32) {
                 const int jj = jb + lane;
                 __syncwarp();
-                stage[w][lane] = jj < j1 ? b.A32[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                stage[lane] = jj < j1 ? b.A32[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
                 __syncwarp();
                 if (!act) continue;
                 const int cnt = min(32, j1 - jb);
@@ -296,7 +294,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbors(Bufs b, const int *
                     const int j = jb + t;
                     uint32_t entry;
                     int tj;
-                    if (j == s || !nb_test(b, I, Ai, ti, Ri, j, stage[w][t], sx, sy, sz, entry, tj)) continue;
+                    if (j == s || !nb_test(b, I, Ai, ti, Ri, j, stage[t], sx, sy, sz, entry, tj)) continue;
                     rig |= (tj == T_RIGID);
                     if (pair_owned(s, j, base)) {
                         if (nf + m < cap) col[(long long)nf * Np] = (int)entry;
@@ -326,6 +324,325 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbors(Bufs b, const int *
         b.nfirst[s] = min(nf, min(cap, b.capown));
         b.ncnt[s] = min(n, cap);
         b.nbflag[s] = rig ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(NB_WARPS * 32) k_neighbors(Bufs b, const int *gate)
+{
+    GATE;
+    __shared__ float4 stage[NB_WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * NB_WARPS + w;
+    if (c >= b.ncell_total) return;   // the whole warp
+    const int s0 = b.cstart[c], s1 = b.cstart[c + 1];
+    if (s0 == s1) return;
+    nb_scan_cell(b, c, s0, s1, stage[w], lane);
+}
+
+// Half-size cells hold about 11 particles, too few for one lane per particle.
+// This form gives the lanes candidates instead.
+//
+// A warp takes one cell. It flattens the candidates of the cell's
+// neighbour cells (ascending key, then slot), and takes the cell's particles
+// in groups of NG_G. For each group:
+// * Every batch of 32 candidates is tested against the group's bounding box,
+//   widened to the list radius. About half of the 125-cell stencil survives
+//   for a half cell, against 27 cells' worth of candidates for a full cell.
+// * The survivors are compacted in order into a staging area.
+// * Each full stage of 32 runs one round per particle of the group: every
+//   lane tests its candidate against that particle. Ballots place the hits in
+//   scan order.
+// * The group's lists are collected in shared memory as 16-bit entries (the
+//   neighbour cell in the table, the offset in the cell, the contact-only
+//   flag), owned entries from the front and the others from the back.
+// * The lists are then written out row by row, the group's particles side by
+//   side (32 / 8 = 4 rows per store for a full group), instead of one
+//   scattered column entry per lane.
+// A cell with a neighbour cell of more than 256 particles (beyond the 8-bit
+// offset) is scanned by the lane-per-particle routine instead.  Either way
+// the lists come out exactly as the lane-per-particle kernel writes them from
+// the same cells: the same entries in the same order, the same counts and
+// flags.
+constexpr int NG_G = 8;        // particles per group
+constexpr int NG_TAB = 128;    // neighbour-cell table entries (>= ADJ)
+constexpr int NG_STAGE = 64;   // staged candidates (one batch on top of a partial stage)
+constexpr int NG_MAX_WARPS = 4;
+constexpr int NG_OFF = 256;    // largest neighbour cell of the 16-bit entries
+
+struct NgShared {
+    int pre[NG_TAB + 1];       // candidates before each neighbour cell (flattened index)
+    int js[NG_TAB];            // first slot of each neighbour cell
+    int code[NG_TAB];          // its offset code (ox+2) + 5 (oy+2) + 25 (oz+2)
+    float4 sa[NG_STAGE];       // staged candidates: record,
+    int sj[NG_STAGE];          //   slot,
+    int sq[NG_STAGE];          //   neighbour cell << 8 | offset in it,
+    float sr[NG_STAGE];        //   radius where it can be a contact partner, else 0
+    float4 ai[NG_G];           // the group's records,
+    float ri[NG_G];            //   rigid radii
+};
+
+// list-buffer row stride (16-bit entries): stride % 64 == 8 puts the rows
+// of consecutive particles 16 bytes (4 banks) apart
+__host__ __device__ constexpr int ng_stride(int cap) { return cap + ((72 - cap % 64) % 64); }
+__host__ __device__ constexpr size_t ng_head() { return (sizeof(NgShared) + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t ng_warp_bytes(int cap)
+{
+    return ng_head() + (size_t)NG_G * ng_stride(cap) * sizeof(uint16_t);
+}
+
+__global__ void __launch_bounds__(NG_MAX_WARPS * 32) k_neighbors_grp(Bufs b, const int *gate)
+{
+    GATE;
+    extern __shared__ __align__(16) unsigned char ng_smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int c = blockIdx.x * nw + w;
+    if (c >= b.ncell_total) return;   // the whole warp
+    const int s0 = b.cstart[c], s1 = b.cstart[c + 1];
+    if (s0 == s1) return;
+    const int cap = b.cap, stride = ng_stride(cap);
+    unsigned char *mine = ng_smem + (size_t)w * ng_warp_bytes(cap);
+    NgShared &S = *reinterpret_cast<NgShared *>(mine);
+    uint16_t *buf = reinterpret_cast<uint16_t *>(mine + ng_head());
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+
+    // neighbour-cell table (valid codes are a prefix of the row)
+    const int *adj = b.cell_adj + (long long)c * ADJ;
+    int total = 0, nq = 0;
+    bool fat = false;
+    for (int q0 = 0; q0 < ADJ; q0 += 32) {
+        const int q = q0 + lane;
+        const int code = q < ADJ ? adj[q] : -1;
+        int cnt = 0, js = 0;
+        if (code >= 0) {
+            const int key = code >> 7;
+            js = b.cstart[key];
+            cnt = b.cstart[key + 1] - js;
+        }
+        fat = fat || __any_sync(FULL, cnt > NG_OFF);
+        int v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += t;
+        }
+        if (code >= 0) {
+            S.pre[q] = total + v - cnt;
+            S.js[q] = js;
+            S.code[q] = code & 127;
+        }
+        total += __shfl_sync(FULL, v, 31);
+        const unsigned vm = __ballot_sync(FULL, code >= 0);
+        nq += __popc(vm);
+        if (vm != FULL) break;
+    }
+    if (fat) {
+        // the list buffer serves as the routine's stage (512 bytes)
+        nb_scan_cell(b, c, s0, s1, reinterpret_cast<float4 *>(buf), lane);
+        return;
+    }
+    if (lane == 0) S.pre[nq] = total;
+    __syncwarp();
+
+    const Inst &I = b.inst[b.pinst[b.perm[s0]]];   // a cell belongs to one instance
+    const int base = b.cstart[I.cell_base];           // first slot of the instance
+    const long long Np = b.Npad;
+    const float rb2_box = I.rb2f * 1.001f;   // conservative: the pair test decides
+    const float two_hs = (float)(2.0 * I.half_skin);
+    const float cx = I.csf[0], cy = I.csf[1], cz = I.csf[2];
+    const float BIG = 3.0e38f;
+
+    for (int g0 = s0; g0 < s1; g0 += NG_G) {
+        const int P = min(NG_G, s1 - g0);
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        int t = T_FLUID;
+        float r = 0.f;
+        if (lane < P) {
+            a = b.A32[g0 + lane];
+            t = b.stype[g0 + lane];
+            r = (t == T_RIGID) ? (float)b.R[b.perm[g0 + lane]] : 0.f;
+            S.ai[lane] = a;
+            S.ri[lane] = r;
+        }
+        float lx = lane < P ? a.x : BIG, ly = lane < P ? a.y : BIG, lz = lane < P ? a.z : BIG;
+        float hx = lane < P ? a.x : -BIG, hy = lane < P ? a.y : -BIG, hz = lane < P ? a.z : -BIG;
+        float rg = r;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {   // lanes >= NG_G hold the neutral values
+            lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
+            rg = fmaxf(rg, __shfl_xor_sync(FULL, rg, o));
+        }
+        lx = __shfl_sync(FULL, lx, 0); ly = __shfl_sync(FULL, ly, 0); lz = __shfl_sync(FULL, lz, 0);
+        hx = __shfl_sync(FULL, hx, 0); hy = __shfl_sync(FULL, hy, 0); hz = __shfl_sync(FULL, hz, 0);
+        rg = __shfl_sync(FULL, rg, 0);
+        const bool grp_rigid = __any_sync(FULL, lane < P && t == T_RIGID);
+        __syncwarp();
+
+        int nf[NG_G], m[NG_G];
+        bool rig[NG_G];
+#pragma unroll
+        for (int p = 0; p < NG_G; ++p) { nf[p] = 0; m[p] = 0; rig[p] = false; }
+
+        // one round per particle over the first nv staged candidates
+        auto rounds = [&](int nv) {
+            float4 Aj = make_float4(0.f, 0.f, 0.f, 0.f);
+            int j = -1, tj = T_FLUID;
+            uint32_t e16 = 0;
+            float rj = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+            if (lane < nv) {
+                Aj = S.sa[lane];
+                j = S.sj[lane];
+                rj = S.sr[lane];
+                e16 = (uint32_t)S.sq[lane];
+                const int oc = S.code[e16 >> 8];
+                tj = unpack_type(__float_as_uint(Aj.w));
+                sx = (float)(oc % 5 - 2) * cx;
+                sy = (float)((oc / 5) % 5 - 2) * cy;
+                sz = (float)(oc / 25 - 2) * cz;
+            }
+#pragma unroll
+            for (int p = 0; p < NG_G; ++p) {
+                if (p < P) {
+                    const float4 Ai = S.ai[p];
+                    const int ti = unpack_type(__float_as_uint(Ai.w));
+                    const int s = g0 + p;
+                    bool hit = false;
+                    uint32_t entry = e16;
+                    if (lane < nv && j != s) {
+                        const float dx = (Ai.x - Aj.x) - sx, dy = (Ai.y - Aj.y) - sy, dz = (Ai.z - Aj.z) - sz;
+                        const float r2f = dx * dx + dy * dy + dz * dz;
+                        if (r2f < I.rb2f) {
+                            hit = true;
+                        } else if (ti == T_RIGID && tj == T_RIGID) {
+                            const float lim = (S.ri[p] + rj + two_hs) * 1.0001f;
+                            entry |= 0x8000u;   // contact range only
+                            hit = r2f < lim * lim;
+                        }
+                    }
+                    const bool own = hit && pair_owned(s, j, base);
+                    const unsigned mh = __ballot_sync(FULL, hit), mo = __ballot_sync(FULL, own);
+                    const unsigned mr = __ballot_sync(FULL, hit && tj == T_RIGID);
+                    // rank in scan order decides whether the entry fits, as
+                    // the per-particle scan writes while nf + m < cap
+                    if (hit && nf[p] + m[p] + __popc(mh & lt) < cap) {
+                        const int pos = own ? nf[p] + __popc(mo & lt) : cap - 1 - (m[p] + __popc(mh & ~mo & lt));
+                        buf[p * stride + pos] = (uint16_t)entry;
+                    }
+                    nf[p] += __popc(mo);
+                    m[p] += __popc(mh & ~mo);
+                    rig[p] = rig[p] || (mr != 0u);
+                }
+            }
+            __syncwarp();
+        };
+
+        int nst = 0, qc = 0;
+        for (int f0 = 0; f0 < total; f0 += 32) {
+            const int f = f0 + lane;
+            bool keep = false;
+            float4 Aj = make_float4(0.f, 0.f, 0.f, 0.f);
+            int j = 0, eq = 0, q = qc;
+            float rj = 0.f;
+            if (f < total) {
+                while (S.pre[q + 1] <= f) ++q;
+                const int off = f - S.pre[q];
+                j = S.js[q] + off;
+                eq = (q << 8) | off;
+                const int oc = S.code[q];
+                Aj = b.A32[j];
+                const int tj = unpack_type(__float_as_uint(Aj.w));
+                const float px = Aj.x + (float)(oc % 5 - 2) * cx, py = Aj.y + (float)((oc / 5) % 5 - 2) * cy,
+                            pz = Aj.z + (float)(oc / 25 - 2) * cz;
+                const float ex = fmaxf(fmaxf(lx - px, px - hx), 0.f), ey = fmaxf(fmaxf(ly - py, py - hy), 0.f),
+                            ez = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
+                const float d2 = ex * ex + ey * ey + ez * ez;
+                float lim2 = rb2_box;
+                if (grp_rigid && tj == T_RIGID) {
+                    rj = (float)b.R[b.perm[j]];
+                    const float L = (rg + rj + two_hs) * (1.0001f * 1.0005f);
+                    lim2 = fmaxf(lim2, L * L);
+                }
+                keep = d2 < lim2;
+            }
+            qc = __shfl_sync(FULL, q, 31);   // the cell of this batch's last candidate
+            const unsigned km = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int pos = nst + __popc(km & lt);
+                S.sa[pos] = Aj;
+                S.sj[pos] = j;
+                S.sq[pos] = eq;
+                S.sr[pos] = rj;
+            }
+            nst += __popc(km);
+            __syncwarp();
+            if (nst >= 32) {
+                rounds(32);
+                // move the remainder to the front of the stage
+                const bool mv = lane < nst - 32;
+                float4 ma;
+                int mj = 0, mq = 0;
+                float mr = 0.f;
+                if (mv) {
+                    ma = S.sa[32 + lane];
+                    mj = S.sj[32 + lane];
+                    mq = S.sq[32 + lane];
+                    mr = S.sr[32 + lane];
+                }
+                __syncwarp();
+                if (mv) {
+                    S.sa[lane] = ma;
+                    S.sj[lane] = mj;
+                    S.sq[lane] = mq;
+                    S.sr[lane] = mr;
+                }
+                nst -= 32;
+                __syncwarp();
+            }
+        }
+        if (nst > 0) rounds(nst);
+
+        // counts and flags of the group's particles
+        int mynf = 0, mym = 0;
+        bool myrig = false;
+#pragma unroll
+        for (int p = 0; p < NG_G; ++p)
+            if (lane == p) { mynf = nf[p]; mym = m[p]; myrig = rig[p]; }
+        int myn = 0;
+        if (lane < P) {
+            const int s = g0 + lane;
+            myn = mynf + mym;
+            if (mynf > b.capown || mym > b.capown) atomicOr(b.err, ERR_PAIR_CAP);
+            if (myn > cap) atomicOr(b.err, ERR_NBR_CAP);
+            b.nfirst[s] = min(mynf, min(cap, b.capown));
+            b.ncnt[s] = min(myn, cap);
+            b.nbflag[s] = myrig ? 1 : 0;
+        }
+        int maxn = lane < P ? min(myn, cap) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(FULL, maxn, o));
+        // write-out: lane = (row kr, particle p), the group's particles side
+        // by side; without overflow the back region [cap - m, cap) moves
+        // down to [nf, n) as it is
+        const int L = P > 4 ? 8 : (P > 2 ? 4 : P);   // lanes per row (P = 1, 2, 4 or 8 after rounding up)
+        const int lsh = L == 8 ? 3 : (L == 4 ? 2 : L - 1);
+        const int p = lane & (L - 1), kr = lane >> lsh, R = 32 >> lsh;
+        const int pnf = __shfl_sync(FULL, mynf, p), pm = __shfl_sync(FULL, mym, p);
+        const int pn = pnf + pm, pcnt = min(pn, cap);
+        const bool wp = p < P;
+        for (int k0 = 0; k0 < maxn; k0 += R) {
+            const int k = k0 + kr;
+            if (wp && k < pcnt) {
+                const int src = (pn > cap || k < pnf) ? k : cap - pm + (k - pnf);
+                const uint32_t e = buf[p * stride + src];
+                const int slot = S.js[(e >> 8) & 127u] + (int)(e & 255u);
+                b.nbr[(long long)k * Np + g0 + p] = (int)((uint32_t)slot | ((e & 0x8000u) ? NB_FAR : 0u));
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -398,6 +715,16 @@ __global__ void k_build_done(Bufs b, const int *gate)
 // ---------------------------------------------------------------- launchers
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// dynamic shared memory of the lane-per-candidate list kernel: at least one
+// warp's buffers at the largest list capacity
+constexpr size_t NG_SMEM_MAX = 200 * 1024;
+static_assert(ng_warp_bytes(SDPD_MAX_NEIGHBORS) <= NG_SMEM_MAX, "list buffers of one warp exceed the limit");
+
+void init_cell_kernels()
+{
+    cudaFuncSetAttribute(k_neighbors_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NG_SMEM_MAX);
+}
+
 void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, cudaStream_t st)
 {
     const int nc = b.ncell_total;
@@ -411,7 +738,13 @@ void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, c
         k_scatter<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
         k_rank<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
         k_gather<<<nblk(b.N, 256), 256, 0, st>>>(b, precision, gate);
-        k_neighbors<<<nblk(nc, NB_WARPS), NB_WARPS * 32, 0, st>>>(b, gate);
+        if (b.cell_sub == 2) {
+            const size_t wb = ng_warp_bytes(b.cap);
+            const int ngw = (int)std::min<size_t>(NG_MAX_WARPS, NG_SMEM_MAX / wb);
+            k_neighbors_grp<<<nblk(nc, ngw), ngw * 32, ngw * wb, st>>>(b, gate);
+        } else {
+            k_neighbors<<<nblk(nc, NB_WARPS), NB_WARPS * 32, 0, st>>>(b, gate);
+        }
         if (need_rev) k_rev<<<nblk(b.N, 128), 128, 0, st>>>(b, gate);
     }
     k_build_done<<<1, 1, 0, st>>>(b, gate);

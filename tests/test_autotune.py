@@ -14,14 +14,19 @@ def test_search_picks_fastest_and_skips_nothing_required():
 
     def fake(setting):
         t = mode_cost[setting["newton3"]] - 10 * setting["skin"] + abs(setting["block"] - 128) / 64 \
-            + 0.1 * setting.get("tpp", 1)
+            + 0.1 * setting.get("tpp", 1) + 0.05 * setting.get("cells", 1)
         times[tuple(sorted(setting.items()))] = t
         return t
 
     best, table = autotune.search(fake)
-    assert best == {"newton3": 1, "skin": 0.12, "block": 128, "tpp": 1}
+    assert best == {"newton3": 1, "skin": 0.12, "block": 128, "tpp": 1, "cells": 1}
     # several lanes per particle only for the direct pass, default block and skin
     assert {(r["newton3"], r["block"], r["skin"]) for r in table if r["tpp"] != 1} == {(0, 128, 0.03)}
+    # half-size cells: one lane per particle, default block, the smaller skins
+    half = [r for r in table if r["cells"] == 2]
+    assert {(r["tpp"], r["block"]) for r in half} == {(1, 128)}
+    assert {r["skin"] for r in half} == {0.0, 0.03, 0.06}
+    assert {r["newton3"] for r in half} == {0, 1, 5}
     assert min(r["ms"] for r in table) == pytest.approx(fake(best))
     assert {r["newton3"] for r in table} == {0, 1, 5}
     # asked for, the pair stream is sampled at the two larger blocks and
@@ -38,7 +43,7 @@ def test_search_picks_fastest_and_skips_nothing_required():
 
 def test_search_ignores_unusable_settings():
     best, table = autotune.search(lambda s: None if s["block"] == 64 else 1.0 + s["skin"] + s["tpp"])
-    assert best["block"] != 64 and best["skin"] == 0.0
+    assert best["block"] != 64 and best["skin"] == 0.0 and best["cells"] == 1
 
 
 def test_cache_roundtrip(tmp_path):
@@ -57,7 +62,8 @@ def test_tune_on_gpu(tmp_path):
     from paper_2002_03120_gb300 import cases
     case = cases.sedimentation(nx=16, ny=16, nz=32)
     cache = str(tmp_path / "tune.json")
-    cand = {"newton3": (1, 0, 2), "skin": (0.0, 0.03, 0.06), "block": (128, 256), "tpp": (1, 2)}
+    cand = {"newton3": (1, 0, 2), "skin": (0.0, 0.03, 0.06), "block": (128, 256), "tpp": (1, 2),
+            "cells": (1, 2)}
     best = autotune.tune(case, precision=B.SDPD_PREC_SPLIT, steps=3, warmup=2, cache_path=cache,
                          candidates=cand)
     assert best["block"] in (128, 256) and best["newton3"] in (0, 1, 2)
