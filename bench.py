@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--max-neighbors", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (force variant, skin, block size) and use the defaults")
+    ap.add_argument("--cells", type=int, default=0, choices=[0, 1, 2],
+                    help="cell factor of the neighbour search (1 full, 2 half-size cells); "
+                         "0: the autotuner's choice (1 with --no-tune)")
     a = ap.parse_args()
     if a.precision == "auto":
         a.precision = "split" if a.workload in ("batch", "dambreak") else "fp64"
@@ -184,6 +187,9 @@ def time_graph_path(case, precision, args, local, stream, flush, ws):
     if setting:
         from paper_2002_03120_gb300 import autotune
         autotune.apply(sim, setting)
+    if args.cells:
+        sim.set_cell_factor(args.cells)
+        setting = dict(setting or {}, cells=args.cells)
     sim.build_cells(stream)
     torch.cuda.synchronize()
     pairs = sim.count_pairs()
@@ -213,6 +219,10 @@ def time_graph_path(case, precision, args, local, stream, flush, ws):
     for _ in range(5):
         sim.build_cells(stream)
         dms.append(_timed(stream, lambda: sim.compute_density(stream), flush))
+    # the list build alone (counting sort, mirrors, lists; reverse index for
+    # the Newton-3 passes), forced
+    bms = [_timed(stream, lambda: sim.build_cells(stream), flush) for _ in range(5)]
+    sim.compute_density(stream)
     sim.couple_drag(stream)   # leave the stage sequence complete
     torch.cuda.synchronize()
     # the HBM-bound update kernel alone (velocity Verlet, velver 1)
@@ -234,6 +244,7 @@ def time_graph_path(case, precision, args, local, stream, flush, ws):
     mobile = int(sum(int(np.sum(c["type"] <= 1)) for c in sim.cases))
     out = dict(pairs=pairs, ms=float(sum(ms)), per_step=ms, kernels=kernels,
                force_ms=float(np.median(fms)), density_ms=float(np.median(dms)),
+               build_ms=float(np.median(bms)),
                e2e_ms=float(np.mean(e2e_ms)), integrate_ms=float(np.median(ims)), mobile=mobile,
                setting=setting, e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N,
                instances=len(sim.cases))
@@ -612,6 +623,10 @@ def main():
                          "pair_evals_per_s": pairs / (main_r["density_ms"] / 1e3),
                          "note": "density + EOS (+ filter or reinitialisation where the workload "
                                  "has them) after a list build, L2 flushed, events on the stream"},
+        "list_build": {"ms_per_build": main_r["build_ms"],
+                       "note": "one forced build (cell sort, mirrors, neighbour lists, reverse index "
+                               "where the force variant needs it), L2 flushed, events on the stream; "
+                               "inside the timed steps builds run only when the skin is exceeded"},
         "step_ms": {"min": float(np.min(main_r["per_step"])), "median": float(np.median(main_r["per_step"])),
                     "max": float(np.max(main_r["per_step"]))},
         "gpu_launches": main_r["kernels"] * args.steps,

@@ -940,9 +940,30 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
     write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, P.lev);
 }
 
-template <class R, bool REUSE>
-__device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s, uint32_t step, bool fill)
+// 16-byte asynchronous copy global -> shared, cached in L1 (PTX cp.async,
+// sm_80 and later; measured faster here than the L2-only form), and its
+// commit / wait
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory ring of the async variant: per thread DEPTH stages of the
+// partner's B, C, D records, thread-minor (rec[stage][record][thread]) so a
+// warp's 16-byte accesses fall on consecutive banks.
+constexpr int LEAN_BLOCK = 128;
+template <int DEPTH> struct LeanRing {
+    float4 rec[DEPTH][3][LEAN_BLOCK];
+};
+
+template <class R, bool REUSE, int DEPTH = 0>
+__device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s, uint32_t step, bool fill,
+                                                      LeanRing<DEPTH ? DEPTH : 1> *ring = nullptr)
+{
+    constexpr bool ASYNC = DEPTH > 0;
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
     if (s >= b.N) return;
@@ -969,7 +990,46 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
     T4 zan;
     T2 zbn;
     if (REUSE && P.noise && n > 0) { zan = ld_stream(zA + s); zbn = ld_stream(zB + s); }
+    const int lt = threadIdx.x;
+    // async ring: the records of entry k + DEPTH - 1 go in flight while entry
+    // k is evaluated; one commit group per entry keeps the wait count fixed
+    auto request = [&](int kk, int jj) {
+        if constexpr (ASYNC) {
+            if (kk < n) {
+                const int st = kk % DEPTH;
+                cp_async16(&ring->rec[st][0][lt], Bm + jj);
+                cp_async16(&ring->rec[st][1][lt], Cm + jj);
+                cp_async16(&ring->rec[st][2][lt], Dm + jj);
+            }
+            cp_async_commit();
+        }
+    };
+    // entries 0 .. DEPTH-2 requested before the loop (0 and 1 are jn, jnn);
+    // jq: the list entry DEPTH - 1 ahead, the next to request
+    int jq = 0;
+    if constexpr (ASYNC) {
+        request(0, jn);
+        if constexpr (DEPTH > 2) request(1, jnn);
+#pragma unroll
+        for (int d = 2; d < DEPTH; ++d) {
+            const int e = d < n ? ld_stream(nb + (long long)d * Np) : 0;
+            if (d + 1 < DEPTH) request(d, e);
+            else jq = e;
+        }
+    }
     for (int k = 0; k < n; ++k) {
+        if constexpr (ASYNC) {
+            // the partner DEPTH - 1 entries ahead, whether or not it is within
+            // h, into the stage of entry k - 1, whose copies are complete
+            // first (an entry beyond h is never waited for at its use)
+            cp_async_wait<DEPTH - 1>();
+            if constexpr (DEPTH == 2) {
+                request(k + 1, jnn);
+            } else {
+                request(k + DEPTH - 1, jq);
+                if (k + DEPTH < n) jq = ld_stream(nb + (long long)(k + DEPTH) * Np);
+            }
+        }
         const int j = jn;
         const T4 Aj = An;
         T4 za;
@@ -995,7 +1055,18 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
             }
             continue;
         }
-        const T4 Bj = Bm[j], Cj = Cm[j], Dj = Dm[j];
+        T4 Bj, Cj, Dj;
+        if constexpr (ASYNC) {
+            cp_async_wait<DEPTH - 1>();   // this entry's group is complete
+            const int st = k % DEPTH;
+            Bj = ring->rec[st][0][lt];
+            Cj = ring->rec[st][1][lt];
+            Dj = ring->rec[st][2][lt];
+        } else {
+            Bj = Bm[j];
+            Cj = Cm[j];
+            Dj = Dm[j];
+        }
         R ox, oy, oz, ce, ex, ey, ez, q, om;
         Z6<R> z;
         int zmode = 0;
@@ -1034,6 +1105,7 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
         ty = add_rn(ty, hy);
         tz = add_rn(tz, hz);
     }
+    if constexpr (ASYNC) cp_async_wait<0>();   // nothing left in flight into the ring
     write_fluid_force<R>(b, I, gi, fx, fy, fz, tx, ty, tz, P.lev);
 }
 
@@ -1041,9 +1113,14 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
 // fetched ahead (its other records are loaded after the r < h decision):
 // fewer registers, so more warps per SM hide the loads instead (force mode
 // 5; the same terms in the same order, so the same bits as force_fluid_slot).
-template <class R, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_force_fluid_lean(Bufs b, int velver)
+template <class R, int MINB, int DEPTH = 0>
+__global__ void __launch_bounds__(LEAN_BLOCK, MINB) k_force_fluid_lean(Bufs b, int velver)
 {
+    LeanRing<DEPTH ? DEPTH : 1> *ring = nullptr;
+    if constexpr (DEPTH > 0) {
+        __shared__ LeanRing<DEPTH ? DEPTH : 1> ring_s;
+        ring = &ring_s;
+    }
     const uint32_t step = (uint32_t)(*b.step);
     const bool fill = b.use_cache && velver == 1;
     const bool reuse = b.use_cache && velver == 2 && *b.cache_epoch == *b.list_epoch &&
@@ -1055,10 +1132,10 @@ __global__ void __launch_bounds__(128, MINB) k_force_fluid_lean(Bufs b, int velv
     }
     if (reuse) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-            force_fluid_slot_lean<R, true>(b, base + (threadIdx.x & 31), step, false);
+            force_fluid_slot_lean<R, true, DEPTH>(b, base + (threadIdx.x & 31), step, false, ring);
     } else {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-            force_fluid_slot_lean<R, false>(b, base + (threadIdx.x & 31), step, fill);
+            force_fluid_slot_lean<R, false, DEPTH>(b, base + (threadIdx.x & 31), step, fill, ring);
     }
 }
 
@@ -2061,9 +2138,16 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
             k_force_gather<double, true><<<nblk(b.N, bs), bs, 0, st>>>(b);
         }
     } else if (newton3 == 5) {
-        // registers capped for five 128-thread blocks per SM (20 warps)
-        if (precision == SDPD_PREC_SPLIT)
-            k_force_fluid_lean<float, 5><<<persistent_grid(k_force_fluid_lean<float, 5>, 128, b.N), 128, 0, st>>>(b, velver);
+        // registers capped for five 128-thread blocks per SM (20 warps); the
+        // first evaluation (normals drawn) with the partners' records in an
+        // async shared-memory ring, the second (normals read back from the
+        // cache, far less arithmetic per pair) without: measured faster each
+        if (precision == SDPD_PREC_SPLIT && velver == 1)
+            k_force_fluid_lean<float, 5, 2><<<persistent_grid(k_force_fluid_lean<float, 5, 2>, LEAN_BLOCK, b.N),
+                                              LEAN_BLOCK, 0, st>>>(b, velver);
+        else if (precision == SDPD_PREC_SPLIT)
+            k_force_fluid_lean<float, 5><<<persistent_grid(k_force_fluid_lean<float, 5>, LEAN_BLOCK, b.N),
+                                           LEAN_BLOCK, 0, st>>>(b, velver);
         else
             k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b, velver);
     } else if (b.tpp == 2 || b.tpp == 4) {

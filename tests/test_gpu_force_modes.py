@@ -5,8 +5,8 @@ context):
 * the pair stream (modes 2 and 3: the direct pass with the pairs within h
   compacted through shared memory and evaluated 32 at a time) and the lean
   direct pass (mode 5: fewer registers, the partner's records loaded after
-  the r < h decision) add the same terms in the same order as the direct
-  pass (mode 0);
+  the r < h decision, at velver 1 through an async shared-memory ring) add
+  the same terms in the same order as the direct pass (mode 0);
 * the Newton-3 pass with pushed results (mode 4) hands the partner the same
   bits as the one whose partner rebuilds them (mode 1).
 Each also matches the oracle within the force tolerance."""
