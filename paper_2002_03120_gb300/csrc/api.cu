@@ -814,7 +814,7 @@ sdpd_status sdpd_compute_density(sdpd_ctx *c, void *stream)
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
     (void)cudaGetLastError();  // launch errors below are this call's own
     if (!c->cells_valid) return fail(SDPD_E_STATE, "sdpd_build_cells must precede sdpd_compute_density");
-    launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), nullptr, (cudaStream_t)stream);
+    launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1) | (c->any_artvis << 2), half_pairs(c->newton3), nullptr, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     c->density_valid = true;
     return SDPD_OK;
@@ -874,7 +874,7 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         c->density_valid = false;
     }
     if (!c->density_valid) {
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), nullptr, st);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1) | (c->any_artvis << 2), half_pairs(c->newton3), nullptr, st);
         c->density_valid = true;
     }
     if (!c->graph) {
@@ -888,12 +888,12 @@ sdpd_status sdpd_step(sdpd_ctx *c, long long n_steps, void *stream)
         // at velver 1 only after such a build, at velver 2 always
         cudaStream_t cs = c->cap_stream;
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), c->b.fresh, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1) | (c->any_artvis << 2), half_pairs(c->newton3), c->b.fresh, cs);
         launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 1, c->newton3, cs);
         launch_integrate(c->b, c->precision, 1, c->any_artvis, cs);
         enqueue_build(c, cs, c->b.need_build);
-        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1), half_pairs(c->newton3), nullptr, cs);
+        launch_density(c->b, c->precision, c->any_filter | (c->any_reinit << 1) | (c->any_artvis << 2), half_pairs(c->newton3), nullptr, cs);
         launch_drag(c->b, c->precision, cs);
         launch_forces(c->b, c->precision, 2, c->newton3, cs);
         launch_integrate(c->b, c->precision, 2, c->any_artvis, cs);

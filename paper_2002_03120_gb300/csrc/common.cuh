@@ -291,26 +291,26 @@ __device__ __forceinline__ void pair_normals(uint32_t gi, uint32_t gj, uint32_t 
 // Geometry constants of an instance held in registers for the pair loop.
 template <class R> struct Geo;
 template <> struct Geo<float> {
-    bool p0, p1, p2;
     int n0, n1, n2, dm;   // dm: the farthest neighbour cell of the stencil (1 or 2)
     float c0, c1, c2;
     float glo, ghi;   // r^2 guard band (copied: a store in a pair loop may not
                       // force them to be reloaded from the instance table)
     __device__ __forceinline__ explicit Geo(const Inst &I)
-        : p0(I.periodic[0]), p1(I.periodic[1]), p2(I.periodic[2]), n0(I.nc[0]), n1(I.nc[1]),
-          n2(I.nc[2]), dm(I.sub), c0(I.csf[0]), c1(I.csf[1]), c2(I.csf[2]), glo(I.guard_lo),
-          ghi(I.guard_hi) {}
+        : n0(I.nc[0]), n1(I.nc[1]), n2(I.nc[2]), dm(I.sub), c0(I.csf[0]), c1(I.csf[1]), c2(I.csf[2]),
+          glo(I.guard_lo), ghi(I.guard_hi) {}
     __device__ __forceinline__ void disp(const float4 &Ai, const float4 &Aj, float &rx, float &ry,
                                          float &rz) const
     {
         const uint32_t bi = __float_as_uint(Ai.w), bj = __float_as_uint(Aj.w);
         int d0 = unpack_cx(bi) - unpack_cx(bj), d1 = unpack_cy(bi) - unpack_cy(bj),
             d2 = unpack_cz(bi) - unpack_cz(bj);
-        // neighbours are at most dm cells apart and periodic axes hold at
-        // least 2 dm + 1 cells, so a larger difference is a wrap
-        if (p0) d0 = d0 > dm ? d0 - n0 : (d0 < -dm ? d0 + n0 : d0);
-        if (p1) d1 = d1 > dm ? d1 - n1 : (d1 < -dm ? d1 + n1 : d1);
-        if (p2) d2 = d2 > dm ? d2 - n2 : (d2 < -dm ? d2 + n2 : d2);
+        // The cells are those of the list build, and a listed pair was at
+        // most dm cells apart then.  A periodic axis holds at least 2 dm + 1
+        // cells, so a larger difference is a wrap.  On a closed axis the
+        // difference never exceeds dm, so the same test needs no flag.
+        d0 = d0 > dm ? d0 - n0 : (d0 < -dm ? d0 + n0 : d0);
+        d1 = d1 > dm ? d1 - n1 : (d1 < -dm ? d1 + n1 : d1);
+        d2 = d2 > dm ? d2 - n2 : (d2 < -dm ? d2 + n2 : d2);
         rx = (Ai.x - Aj.x) + (float)d0 * c0;
         ry = (Ai.y - Aj.y) + (float)d1 * c1;
         rz = (Ai.z - Aj.z) + (float)d2 * c2;
@@ -391,7 +391,8 @@ void set_last_error(const char *msg);
 // gate: nullptr = always build; else build only when *gate != 0
 void launch_build(const Bufs &b, int precision, int need_rev, const int *gate, cudaStream_t st);
 // dflags: bit 0 some instance filters the pressure, bit 1 some instance
-// reinitialises the density
+// reinitialises the density, bit 2 some instance has the artificial viscosity
+// (the density pass then marks the collision candidates)
 void launch_density(const Bufs &b, int precision, int dflags, int newton3, const int *gate, cudaStream_t st);
 void launch_drag(const Bufs &b, int precision, cudaStream_t st);
 // force mode: 0 direct, 1 Newton 3 (half pairs + gather), 2 pair stream

@@ -137,12 +137,30 @@ template <> struct Acc<float> {
     __device__ __forceinline__ void add(float v) { k.add(v); }
     __device__ __forceinline__ double value() const { return k.value(); }
 };
+// The density sum: every term is W(q) <= W(0), and the sum starts at the
+// self term W(0), so |s| >= |v| at every step and the compensation needs no
+// branch (Dekker's fast two-sum error term; the same result as KSum there).
+template <class R> struct PosAcc;
+template <> struct PosAcc<float> {
+    float s, c;
+    __device__ __forceinline__ explicit PosAcc(double v0) : s((float)v0), c(0.f) {}
+    __device__ __forceinline__ void add(float v)
+    {
+        const float t = s + v;
+        c += (s - t) + v;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 template <> struct Acc<double> {
     double s;
     __device__ __forceinline__ explicit Acc(double v0) : s(v0) {}
     // a separate rounding of each term (no multiply-add fused into the sum)
     __device__ __forceinline__ void add(double v) { s = __dadd_rn(s, v); }
     __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct PosAcc<double> : Acc<double> {
+    using Acc<double>::Acc;
 };
 
 // Eq. prtcpres: p = p0 (rho / rho0)^alpha - beta; an integer alpha (7 in
@@ -247,7 +265,7 @@ __device__ __forceinline__ void for_each_entry(const int *__restrict__ nb, long 
     }
 }
 
-template <class R>
+template <class R, bool CLOSE>
 __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const int *gate)
 {
     if (gate && *gate == 0) return;
@@ -259,7 +277,8 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
     const int ti = b.stype[s];
     // mark particles with a mobile neighbour inside the collision radius of
     // the artificial viscosity (a superset: the collision pass decides exactly)
-    const bool want_close = I.artvis && (ti == T_FLUID || ti == T_RIGID);
+    // (CLOSE: some instance of the context has the artificial viscosity)
+    const bool want_close = CLOSE && I.artvis && (ti == T_FLUID || ti == T_RIGID);
     const R close_r2 = (R)(I.artvis_r2f_hi * 1.0001f);
     bool close = false;
     double d;
@@ -272,12 +291,12 @@ __global__ void __launch_bounds__(256) k_density(Bufs b, int any_filter, const i
         const int n = b.ncnt[s];
         const long long Np = b.Npad;
         const R Wc = K<R>::Wc(I), irc = K<R>::inv_rc(I);
-        Acc<R> acc(I.W0);
+        PosAcc<R> acc(I.W0);
         for_each_entry(b.nbr + s, Np, n, A, nullptr, [&](int, uint32_t e, const decltype(Ai) &Aj, double) {
             if (e & NB_FAR) return;
             R rx, ry, rz, r2;
             if (!Rel<R>::get(b, I, geo, Ai, Aj, gi, (int)e, rx, ry, rz, r2)) return;
-            if (want_close && r2 <= close_r2) {
+            if (CLOSE && want_close && r2 <= close_r2) {
                 const int tj = mir_type(Aj);
                 close |= (tj == T_FLUID || tj == T_RIGID);
             }
@@ -2042,7 +2061,7 @@ static unsigned persistent_grid(K kernel, int block, long long N)
 void launch_density(const Bufs &b, int precision, int dflags, int newton3, const int *gate, cudaStream_t st)
 {
     if (!b.N) return;
-    const int any_filter = dflags & 1, any_reinit = (dflags >> 1) & 1;
+    const int any_filter = dflags & 1, any_reinit = (dflags >> 1) & 1, any_artvis = (dflags >> 2) & 1;
     // the density kernels leave the mirrors to a later pass when one follows
     const int defer = any_filter | any_reinit;
     if (precision == SDPD_PREC_FP64 && newton3) {
@@ -2055,14 +2074,16 @@ void launch_density(const Bufs &b, int precision, int dflags, int newton3, const
         }
         if (any_filter) k_filter<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     } else if (precision == SDPD_PREC_SPLIT) {
-        k_density<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
+        if (any_artvis) k_density<float, true><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
+        else k_density<float, false><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
         if (any_reinit) {
             k_reinit<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
             k_reinit_copy<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
         }
         if (any_filter) k_filter<float><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, gate);
     } else {
-        k_density<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
+        if (any_artvis) k_density<double, true><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
+        else k_density<double, false><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, defer, gate);
         if (any_reinit) {
             k_reinit<double><<<nblk(b.N, b.pair_block), b.pair_block, 0, st>>>(b, any_filter, gate);
             k_reinit_copy<<<nblk(b.N, 256), 256, 0, st>>>(b, gate);
