@@ -1930,28 +1930,14 @@ __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
         if (k < n) {
             const int j = (int)(e & ~NB_FAR);
             const T4 Aj = A[j];
-            // FP32 records: the partner's other records are requested with its
-            // position (one gather latency per round instead of two); the
-            // wider FP64 ones after the decision
-            T4 Bj, Cj, Dj;
-            if constexpr (sizeof(R) == 4) {
-                Bj = Bm[j];
-                Cj = Cm[j];
-                Dj = Dm[j];
-            }
             const int tj = mir_type(Aj);
             if (tj == T_FLUID && !(e & NB_FAR)) {
                 // F^C + F^D of the pair (s, j), summed for Eq. F_fpi_PG
                 R rx, ry, rz, r2;
                 if (Rel<R>::get(b, I, geo, Ai, Aj, g, j, rx, ry, rz, r2)) {
-                    if constexpr (sizeof(R) != 4) {
-                        Bj = Bm[j];
-                        Cj = Cm[j];
-                        Dj = Dm[j];
-                    }
                     Z6<R> z;
                     R ox, oy, oz, ce, ex, ey, ez, q, om;
-                    sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, false, 0, z, ox, oy, oz, ce,
+                    sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bm[j], Cm[j], Dm[j], false, 0, z, ox, oy, oz, ce,
                                  ex, ey, ez, q, om);
                     f0 += ox + ce * ex;
                     f1 += oy + ce * ey;
