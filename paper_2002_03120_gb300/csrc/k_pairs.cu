@@ -978,7 +978,10 @@ template <int DEPTH> struct LeanRing {
     float4 rec[DEPTH][3][LEAN_BLOCK];
 };
 
-template <class R, bool REUSE, int DEPTH = 0>
+// DEPTH > 0: the partner's B, C, D records through the async ring (above);
+// PF: instead, fetched one entry ahead into registers with its position
+// (needs 128 registers, the second evaluation only)
+template <class R, bool REUSE, int DEPTH = 0, bool PF = false>
 __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s, uint32_t step, bool fill,
                                                       LeanRing<DEPTH ? DEPTH : 1> *ring = nullptr)
 {
@@ -1006,6 +1009,8 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
     int jn = n > 0 ? ld_stream(nb) : 0;
     int jnn = n > 1 ? ld_stream(nb + Np) : 0;
     T4 An = A[jn];
+    T4 Bn, Cn, Dn;
+    if constexpr (PF) { Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn]; }
     T4 zan;
     T2 zbn;
     if (REUSE && P.noise && n > 0) { zan = ld_stream(zA + s); zbn = ld_stream(zB + s); }
@@ -1051,12 +1056,15 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
         }
         const int j = jn;
         const T4 Aj = An;
+        T4 Bp, Cp, Dp;
+        if constexpr (PF) { Bp = Bn; Cp = Cn; Dp = Dn; }
         T4 za;
         T2 zb;
         if (REUSE) { za = zan; zb = zbn; }
         if (k + 1 < n) {
             jn = jnn;
             An = A[jn];
+            if constexpr (PF) { Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn]; }
             if (REUSE && P.noise) {
                 zan = ld_stream(zA + (long long)(k + 1) * Np + s);
                 zbn = ld_stream(zB + (long long)(k + 1) * Np + s);
@@ -1081,6 +1089,10 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
             Bj = ring->rec[st][0][lt];
             Cj = ring->rec[st][1][lt];
             Dj = ring->rec[st][2][lt];
+        } else if constexpr (PF) {
+            Bj = Bp;
+            Cj = Cp;
+            Dj = Dp;
         } else {
             Bj = Bm[j];
             Cj = Cm[j];
@@ -1132,7 +1144,9 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
 // fetched ahead (its other records are loaded after the r < h decision):
 // fewer registers, so more warps per SM hide the loads instead (force mode
 // 5; the same terms in the same order, so the same bits as force_fluid_slot).
-template <class R, int MINB, int DEPTH = 0>
+// ONLY: 0 every path; 1 only the second evaluation that reads the cached
+// normals (returns at once otherwise); 2 only the paths that draw them
+template <class R, int MINB, int DEPTH = 0, int ONLY = 0, bool PF = false>
 __global__ void __launch_bounds__(LEAN_BLOCK, MINB) k_force_fluid_lean(Bufs b, int velver)
 {
     LeanRing<DEPTH ? DEPTH : 1> *ring = nullptr;
@@ -1149,10 +1163,12 @@ __global__ void __launch_bounds__(LEAN_BLOCK, MINB) k_force_fluid_lean(Bufs b, i
         *b.cache_epoch = *b.list_epoch;
         *b.cache_step = *b.step;
     }
-    if (reuse) {
+    if (ONLY == 1 && !reuse) return;
+    if (ONLY == 2 && reuse) return;
+    if (ONLY != 2 && reuse) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-            force_fluid_slot_lean<R, true, DEPTH>(b, base + (threadIdx.x & 31), step, false, ring);
-    } else {
+            force_fluid_slot_lean<R, true, DEPTH, PF>(b, base + (threadIdx.x & 31), step, false, ring);
+    } else if (ONLY != 1) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
             force_fluid_slot_lean<R, false, DEPTH>(b, base + (threadIdx.x & 31), step, fill, ring);
     }
@@ -2166,9 +2182,19 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
         if (precision == SDPD_PREC_SPLIT && velver == 1)
             k_force_fluid_lean<float, 5, 2><<<persistent_grid(k_force_fluid_lean<float, 5, 2>, LEAN_BLOCK, b.N),
                                               LEAN_BLOCK, 0, st>>>(b, velver);
-        else if (precision == SDPD_PREC_SPLIT)
-            k_force_fluid_lean<float, 5><<<persistent_grid(k_force_fluid_lean<float, 5>, LEAN_BLOCK, b.N),
-                                           LEAN_BLOCK, 0, st>>>(b, velver);
+        else if (precision == SDPD_PREC_SPLIT) {
+            // velver 2: the pass that reads the cached normals, compiled alone
+            // with the partners' records fetched one entry ahead (128
+            // registers, 16 warps per SM), then the drawing pass for the case
+            // where the cache is not valid; each returns at once when the
+            // other one applies
+            k_force_fluid_lean<float, 4, 0, 1, true>
+                <<<persistent_grid(k_force_fluid_lean<float, 4, 0, 1, true>, LEAN_BLOCK, b.N), LEAN_BLOCK, 0, st>>>(
+                    b, velver);
+            cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
+            k_force_fluid_lean<float, 5, 0, 2>
+                <<<persistent_grid(k_force_fluid_lean<float, 5, 0, 2>, LEAN_BLOCK, b.N), LEAN_BLOCK, 0, st>>>(b, velver);
+        }
         else
             k_force_fluid<double><<<persistent_grid(k_force_fluid<double>, bs, b.N), bs, 0, st>>>(b, velver);
     } else if (b.tpp == 2 || b.tpp == 4) {
