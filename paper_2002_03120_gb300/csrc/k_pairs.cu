@@ -58,6 +58,27 @@ __device__ __forceinline__ int mir_type(const float4 &A) { return unpack_type(__
 __device__ __forceinline__ int mir_type(const double4_32a &A) { return (int)A.w; }
 __device__ __forceinline__ uint32_t mir_gid(const float4 &D) { return __float_as_uint(D.w); }
 __device__ __forceinline__ uint32_t mir_gid(const double4_32a &D) { return (uint32_t)D.w; }
+// The density terms of a particle for the pair routine.  FP32 records keep
+// p/d^2 in B.w and 1/d in C.w, next to the velocity and the spin, so that a
+// pass reading no gid (the second evaluation, normals from the cache) needs
+// two records of a partner instead of three; 1/sqrt(d_i d_j) is then formed as
+// sqrt(1/d_i 1/d_j).  FP64 records: D = {p/d^2, 1/d, 1/sqrt(d), gid}.
+__device__ __forceinline__ float mir_pd2(const float4 &B, const float4 &) { return B.w; }
+__device__ __forceinline__ double mir_pd2(const double4_32a &, const double4_32a &D) { return D.x; }
+__device__ __forceinline__ float mir_invd(const float4 &C, const float4 &) { return C.w; }
+__device__ __forceinline__ double mir_invd(const double4_32a &, const double4_32a &D) { return D.y; }
+// om / sqrt(d_i d_j); FP32: x rsqrt(x) of x = 1/d_i 1/d_j > 0 (the hardware
+// reciprocal square root, about 2 ulp, the same in every pass)
+__device__ __forceinline__ float mir_rs(float om, const float4 &Ci, const float4 &, const float4 &Cj, const float4 &)
+{
+    const float x = Ci.w * Cj.w;
+    return om * (x * rsqrtf(x));
+}
+__device__ __forceinline__ double mir_rs(double om, const double4_32a &, const double4_32a &Di, const double4_32a &,
+                                         const double4_32a &Dj)
+{
+    return om * Di.z * Dj.z;
+}
 
 template <class R> struct K;  // kernel constants in precision R
 template <> struct K<float> {
@@ -182,24 +203,24 @@ __device__ __forceinline__ double eos_pressure(const Inst &I, double rho)
     return I.p0 * xa - I.beta_p;
 }
 
-// Per-particle quantities the force pass reads: p/d^2, 1/d, 1/sqrt(d) (in
-// the precision of the pair arithmetic).
+// Per-particle quantities the force pass reads: p/d^2 and 1/d (FP32), also
+// 1/sqrt(d) (FP64), in the precision of the pair arithmetic.
 template <class R>
 __device__ __forceinline__ void finalize_slot(const Bufs &b, long long s, double d, double p)
 {
-    typename Vec<R>::T4 *D = Mir<R>::D(b);
-    typename Vec<R>::T4 o = D[s];
     if constexpr (sizeof(R) == 4) {
+        // FP32 records: p/d^2 beside the velocity, 1/d beside the spin
         const float df = (float)d;
-        o.x = (float)p / (df * df);
-        o.y = 1.0f / df;
-        o.z = rsqrtf(df);
+        b.B32[s].w = (float)p / (df * df);
+        b.C32[s].w = 1.0f / df;
     } else {
+        typename Vec<R>::T4 *D = Mir<R>::D(b);
+        typename Vec<R>::T4 o = D[s];
         o.x = p / (d * d);
         o.y = 1.0 / d;
         o.z = 1.0 / sqrt(d);
+        D[s] = o;
     }
-    D[s] = o;
 }
 
 // Streaming accesses (evict-first in L2): the neighbour lists and the normals
@@ -754,10 +775,10 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R
     ex = rx * ir; ey = ry * ir; ez = rz * ir;
     const R vx = Bi.x - Bj.x, vy = Bi.y - Bj.y, vz = Bi.z - Bj.z;
     const R ev = ex * vx + ey * vy + ez * vz;
-    const R gf = Fk * Di.y * Dj.y;
+    const R gf = Fk * mir_invd(Ci, Di) * mir_invd(Cj, Dj);
     const R c1 = P.A1 * gf;
     // Eq. FijC (central) + the central part of Eq. FijD
-    ce = P.cc * (Di.x + Dj.x) * Fk * (r2 * ir) - P.A2 * gf * ev;
+    ce = P.cc * (mir_pd2(Bi, Di) + mir_pd2(Bj, Dj)) * Fk * (r2 * ir) - P.A2 * gf * ev;
     ox = c1 * vx; oy = c1 * vy; oz = c1 * vz;
     if (!with_rt) return;
     // Eq. FijR
@@ -774,7 +795,7 @@ __device__ __forceinline__ void sdpd_pair(const PairK<R> &P, R rx, R ry, R rz, R
         if (zmode == 0)
             pair_normals<R>(mir_gid(Di), mir_gid(Dj), P.step, P.key0, P.key1, z.z0, z.z1, z.z2, z.z3,
                             z.z4, z.z5);
-        const R rs = om * Di.z * Dj.z;
+        const R rs = mir_rs(om, Ci, Di, Cj, Dj);
         const R sa = P.T1 * rs;
         const R sxy = mul_rn(z.z3, is2), sxz = mul_rn(z.z4, is2), syz = mul_rn(z.z5, is2);
         ce = fma_rn(P.T3 * rs, add_rn(add_rn(z.z0, z.z1), z.z2), ce);
@@ -978,14 +999,16 @@ template <int DEPTH> struct LeanRing {
     float4 rec[DEPTH][3][LEAN_BLOCK];
 };
 
-// DEPTH > 0: the partner's B, C, D records through the async ring (above);
-// PF: instead, fetched one entry ahead into registers with its position
-// (needs 128 registers, the second evaluation only)
-template <class R, bool REUSE, int DEPTH = 0, bool PF = false>
+// DEPTH > 0: the partner's B, C, D records through the async ring (above)
+template <class R, bool REUSE, int DEPTH = 0>
 __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s, uint32_t step, bool fill,
                                                       LeanRing<DEPTH ? DEPTH : 1> *ring = nullptr)
 {
     constexpr bool ASYNC = DEPTH > 0;
+    // FP32, normals from the cache: a partner's D record (its gid) is needed
+    // only for a pair whose normals must be drawn after all (rare), so it is
+    // loaded then
+    constexpr bool LAZY_D = REUSE && sizeof(R) == 4;
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
     if (s >= b.N) return;
@@ -1009,8 +1032,6 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
     int jn = n > 0 ? ld_stream(nb) : 0;
     int jnn = n > 1 ? ld_stream(nb + Np) : 0;
     T4 An = A[jn];
-    T4 Bn, Cn, Dn;
-    if constexpr (PF) { Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn]; }
     T4 zan;
     T2 zbn;
     if (REUSE && P.noise && n > 0) { zan = ld_stream(zA + s); zbn = ld_stream(zB + s); }
@@ -1056,15 +1077,12 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
         }
         const int j = jn;
         const T4 Aj = An;
-        T4 Bp, Cp, Dp;
-        if constexpr (PF) { Bp = Bn; Cp = Cn; Dp = Dn; }
         T4 za;
         T2 zb;
         if (REUSE) { za = zan; zb = zbn; }
         if (k + 1 < n) {
             jn = jnn;
             An = A[jn];
-            if constexpr (PF) { Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn]; }
             if (REUSE && P.noise) {
                 zan = ld_stream(zA + (long long)(k + 1) * Np + s);
                 zbn = ld_stream(zB + (long long)(k + 1) * Np + s);
@@ -1082,21 +1100,17 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
             }
             continue;
         }
-        T4 Bj, Cj, Dj;
+        T4 Bj, Cj, Dj = Di;
         if constexpr (ASYNC) {
             cp_async_wait<DEPTH - 1>();   // this entry's group is complete
             const int st = k % DEPTH;
             Bj = ring->rec[st][0][lt];
             Cj = ring->rec[st][1][lt];
             Dj = ring->rec[st][2][lt];
-        } else if constexpr (PF) {
-            Bj = Bp;
-            Cj = Cp;
-            Dj = Dp;
         } else {
             Bj = Bm[j];
             Cj = Cm[j];
-            Dj = Dm[j];
+            if constexpr (!LAZY_D) Dj = Dm[j];
         }
         R ox, oy, oz, ce, ex, ey, ez, q, om;
         Z6<R> z;
@@ -1105,6 +1119,9 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
         if (REUSE && P.noise && !rig && !isnan(za.x)) {
             z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
             zmode = 1;
+        }
+        if constexpr (LAZY_D) {
+            if (zmode == 0 && P.noise && !rig) Dj = Dm[j];
         }
         sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, !rig, zmode, z, ox, oy, oz, ce, ex, ey, ez,
                      q, om);
@@ -1146,7 +1163,7 @@ __device__ __forceinline__ void force_fluid_slot_lean(const Bufs &b, long long s
 // 5; the same terms in the same order, so the same bits as force_fluid_slot).
 // ONLY: 0 every path; 1 only the second evaluation that reads the cached
 // normals (returns at once otherwise); 2 only the paths that draw them
-template <class R, int MINB, int DEPTH = 0, int ONLY = 0, bool PF = false>
+template <class R, int MINB, int DEPTH = 0, int ONLY = 0>
 __global__ void __launch_bounds__(LEAN_BLOCK, MINB) k_force_fluid_lean(Bufs b, int velver)
 {
     LeanRing<DEPTH ? DEPTH : 1> *ring = nullptr;
@@ -1167,7 +1184,7 @@ __global__ void __launch_bounds__(LEAN_BLOCK, MINB) k_force_fluid_lean(Bufs b, i
     if (ONLY == 2 && reuse) return;
     if (ONLY != 2 && reuse) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
-            force_fluid_slot_lean<R, true, DEPTH, PF>(b, base + (threadIdx.x & 31), step, false, ring);
+            force_fluid_slot_lean<R, true, DEPTH>(b, base + (threadIdx.x & 31), step, false, ring);
     } else if (ONLY != 1) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
             force_fluid_slot_lean<R, false, DEPTH>(b, base + (threadIdx.x & 31), step, fill, ring);
@@ -2183,14 +2200,12 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
             k_force_fluid_lean<float, 5, 2><<<persistent_grid(k_force_fluid_lean<float, 5, 2>, LEAN_BLOCK, b.N),
                                               LEAN_BLOCK, 0, st>>>(b, velver);
         else if (precision == SDPD_PREC_SPLIT) {
-            // velver 2: the pass that reads the cached normals, compiled alone
-            // with the partners' records fetched one entry ahead (128
-            // registers, 16 warps per SM), then the drawing pass for the case
-            // where the cache is not valid; each returns at once when the
-            // other one applies
-            k_force_fluid_lean<float, 4, 0, 1, true>
-                <<<persistent_grid(k_force_fluid_lean<float, 4, 0, 1, true>, LEAN_BLOCK, b.N), LEAN_BLOCK, 0, st>>>(
-                    b, velver);
+            // velver 2: the pass that reads the cached normals, compiled
+            // alone (two partner records per pair, the D record only for a
+            // draw), then the drawing pass for the case where the cache is not
+            // valid; each returns at once when the other one applies
+            k_force_fluid_lean<float, 5, 0, 1>
+                <<<persistent_grid(k_force_fluid_lean<float, 5, 0, 1>, LEAN_BLOCK, b.N), LEAN_BLOCK, 0, st>>>(b, velver);
             cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
             k_force_fluid_lean<float, 5, 0, 2>
                 <<<persistent_grid(k_force_fluid_lean<float, 5, 0, 2>, LEAN_BLOCK, b.N), LEAN_BLOCK, 0, st>>>(b, velver);
