@@ -293,8 +293,8 @@ def force_kernel_name(mode, split):
     if mode in (2, 3):
         return f"k_force_stream<{r}, {mode if split else 1}>"
     if mode == 5 and split:
-        return "k_force_fluid_lean<float, 5, 2>"   # velver 1: with the async record ring
-    return f"k_force_fluid<{r}>"
+        return "k_force_fluid_lean<float, 5, 2, 0>"   # velver 1: with the async record ring
+    return f"k_force_fluid<{r}, 0>"
 
 
 def time_native(args, ws, rank, local):

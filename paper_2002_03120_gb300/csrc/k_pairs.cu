@@ -887,6 +887,9 @@ __device__ __noinline__ void fluid_rigid_pair_call(const Bufs &b, long long s, i
 template <class R, bool REUSE>
 __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uint32_t step, bool fill)
 {
+    // FP32, normals from the cache: a partner's D record (its gid) only for a
+    // pair whose normals must be drawn after all (rare), loaded then
+    constexpr bool LAZY_D = REUSE && sizeof(R) == 4;
     using T4 = typename Vec<R>::T4;
     using T2 = typename Vec2<R>::T2;
     if (s >= b.N) return;
@@ -909,19 +912,22 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
     const long long Np = b.Npad;
     int jn = n > 0 ? ld_stream(nb) : 0;
     int jnn = n > 1 ? ld_stream(nb + Np) : 0;
-    T4 An = A[jn], Bn = Bm[jn], Cn = Cm[jn], Dn = Dm[jn];
+    T4 An = A[jn], Bn = Bm[jn], Cn = Cm[jn], Dn = Di;
+    if constexpr (!LAZY_D) Dn = Dm[jn];
     T4 zan;
     T2 zbn;
     if (REUSE && P.noise && n > 0) { zan = ld_stream(zA + s); zbn = ld_stream(zB + s); }
     for (int k = 0; k < n; ++k) {
         const int j = jn;
-        const T4 Aj = An, Bj = Bn, Cj = Cn, Dj = Dn;
+        const T4 Aj = An, Bj = Bn, Cj = Cn;
+        T4 Dj = Dn;
         T4 za;
         T2 zb;
         if (REUSE) { za = zan; zb = zbn; }
         if (k + 1 < n) {
             jn = jnn;
-            An = A[jn]; Bn = Bm[jn]; Cn = Cm[jn]; Dn = Dm[jn];
+            An = A[jn]; Bn = Bm[jn]; Cn = Cm[jn];
+            if constexpr (!LAZY_D) Dn = Dm[jn];
             if (REUSE && P.noise) {
                 zan = ld_stream(zA + (long long)(k + 1) * Np + s);
                 zbn = ld_stream(zB + (long long)(k + 1) * Np + s);
@@ -946,6 +952,9 @@ __device__ __forceinline__ void force_fluid_slot(const Bufs &b, long long s, uin
         if (REUSE && P.noise && !rig && !isnan(za.x)) {
             z.z0 = za.x; z.z1 = za.y; z.z2 = za.z; z.z3 = za.w; z.z4 = zb.x; z.z5 = zb.y;
             zmode = 1;
+        }
+        if constexpr (LAZY_D) {
+            if (zmode == 0 && P.noise && !rig) Dj = Dm[j];
         }
         sdpd_pair<R>(P, rx, ry, rz, r2, Bi, Ci, Di, Bj, Cj, Dj, !rig, zmode, z, ox, oy, oz, ce, ex, ey, ez,
                      q, om);
@@ -1191,7 +1200,9 @@ __global__ void __launch_bounds__(LEAN_BLOCK, MINB) k_force_fluid_lean(Bufs b, i
     }
 }
 
-template <class R>
+// ONLY as in k_force_fluid_lean: 0 every path, 1 only the pass reading the
+// cached normals, 2 only the drawing paths
+template <class R, int ONLY = 0>
 __global__ void __launch_bounds__(256) k_force_fluid(Bufs b, int velver)
 {
     const uint32_t step = (uint32_t)(*b.step);
@@ -1205,10 +1216,12 @@ __global__ void __launch_bounds__(256) k_force_fluid(Bufs b, int velver)
         *b.cache_step = *b.step;
     }
     // reuse is uniform over the launch
-    if (reuse) {
+    if (ONLY == 1 && !reuse) return;
+    if (ONLY == 2 && reuse) return;
+    if (ONLY != 2 && reuse) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
             force_fluid_slot<R, true>(b, base + (threadIdx.x & 31), step, false);
-    } else {
+    } else if (ONLY != 1) {
         for (long long base = next_warp_slots(b); base < b.N; base = next_warp_slots(b))
             force_fluid_slot<R, false>(b, base + (threadIdx.x & 31), step, fill);
     }
@@ -2222,6 +2235,13 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
             if (b.tpp == 2) k_force_fluid_tpp<double, 2><<<persistent_grid(k_force_fluid_tpp<double, 2>, bs, nt), bs, 0, st>>>(b, velver);
             else k_force_fluid_tpp<double, 4><<<persistent_grid(k_force_fluid_tpp<double, 4>, bs, nt), bs, 0, st>>>(b, velver);
         }
+    } else if (precision == SDPD_PREC_SPLIT && velver == 2) {
+        // the pass reading the cached normals compiled alone (no D records,
+        // no drawing code), then the drawing pass for an invalid cache; each
+        // returns at once when the other one applies
+        k_force_fluid<float, 1><<<persistent_grid(k_force_fluid<float, 1>, bs, b.N), bs, 0, st>>>(b, velver);
+        cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st);
+        k_force_fluid<float, 2><<<persistent_grid(k_force_fluid<float, 2>, bs, b.N), bs, 0, st>>>(b, velver);
     } else if (precision == SDPD_PREC_SPLIT) {
         k_force_fluid<float><<<persistent_grid(k_force_fluid<float>, bs, b.N), bs, 0, st>>>(b, velver);
     } else {
