@@ -1926,25 +1926,58 @@ __device__ __forceinline__ void hist_put(const Bufs &b, int r, int slot, int par
 // neighbours (Eq. F_fpi_PG), DEM + lubrication with the rigid neighbours,
 // wall planes, drag, gravity.  The lanes take the neighbour list in rounds of
 // 32 for the fluid pairs and collect the rigid entries, in list order, in
-// shared memory (dynamic: RPB x cap entries); the rigid pairs then run 32 at
-// a time, so their FP64 arithmetic uses the whole warp.  New history entries
-// go to slots in list order (ballot), so the table is deterministic.
+// shared memory.  A sphere has only a few sphere neighbours, so the block's
+// RPB spheres pool theirs: the pooled pairs run one per thread, RB at a time
+// (their FP64 DEM and lubrication arithmetic on every lane instead of on a
+// few lanes of each warp), each result is kept in shared memory, and each
+// sphere adds its own in list order.  New history entries go to slots in list
+// order, so the table is deterministic.
+struct RigidPairRes {
+    double F[3], T[3], L[3], dn[3];   // DEM force and torque, lubrication, next tangential displacement
+    int partner;                      // gid of a contact partner, -1 without contact
+    int pad;
+};
+__host__ __device__ inline size_t rigid_list_bytes(int cap) { return ((size_t)RPB * cap * sizeof(uint32_t) + 15) / 16 * 16; }
+__host__ __device__ inline size_t rigid_smem_bytes(int cap) { return rigid_list_bytes(cap) + (size_t)RB * sizeof(RigidPairRes); }
+
 template <class R>
 __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
 {
-    extern __shared__ uint32_t rstage[];
+    extern __shared__ __align__(16) unsigned char rsm[];
+    __shared__ double s_x[RPB][3], s_v[RPB][3], s_w[RPB][3], s_R[RPB], s_m[RPB];
+    __shared__ int s_r[RPB], s_inst[RPB], s_nr[RPB], s_pre[RPB + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.x * RPB + warp;
-    if (r >= b.nrigid) return;   // the whole warp
-    uint32_t *rl = rstage + (size_t)warp * b.cap;   // this warp's rigid entries
-    const int g = b.rigid_gid[r];
-    const long long s = b.slot_of[g];
+    const bool live = r < b.nrigid;   // a warp past the end only takes part in the barriers
+    uint32_t *const lists = reinterpret_cast<uint32_t *>(rsm);
+    uint32_t *rl = lists + (size_t)warp * b.cap;   // this warp's rigid entries
+    RigidPairRes *pres = reinterpret_cast<RigidPairRes *>(rsm + rigid_list_bytes(b.cap));
+    const int g = live ? b.rigid_gid[r] : 0;
+    const long long s = live ? b.slot_of[g] : 0;
     const Inst &I = b.inst[b.pinst[g]];
-    const double xi[3] = { b.x[3 * g], b.x[3 * g + 1], b.x[3 * g + 2] };
-    const double vi[3] = { b.v[3 * g], b.v[3 * g + 1], b.v[3 * g + 2] };
-    const double wi[3] = { b.w[3 * g], b.w[3 * g + 1], b.w[3 * g + 2] };
-    const double Ri = b.R[g], mi = b.m[g];
-    const double di = b.sd[s];
+    double xi[3] = { 0.0, 0.0, 0.0 }, vi[3] = { 0.0, 0.0, 0.0 }, wi[3] = { 0.0, 0.0, 0.0 };
+    double Ri = 0.0, mi = 0.0, di = 0.0;
+    if (live) {
+        for (int a = 0; a < 3; ++a) {
+            xi[a] = b.x[3 * g + a];
+            vi[a] = b.v[3 * g + a];
+            wi[a] = b.w[3 * g + a];
+        }
+        Ri = b.R[g];
+        mi = b.m[g];
+        di = b.sd[s];
+        if (lane == 0) {
+            for (int a = 0; a < 3; ++a) {
+                s_x[warp][a] = xi[a];
+                s_v[warp][a] = vi[a];
+                s_w[warp][a] = wi[a];
+            }
+            s_R[warp] = Ri;
+            s_m[warp] = mi;
+            s_r[warp] = r;
+            s_inst[warp] = b.pinst[g];
+        }
+    }
     const bool commit = (velver == 2);
     const long long Np = b.Npad;
     double acc[15];
@@ -1963,7 +1996,7 @@ __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
     const T4 Ai = A[s], Bi = Bm[s], Ci = Cm[s], Di = Dm[s];
     const R Rr = (R)Ri;
     R f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-    const int n = b.ncnt[s];
+    const int n = live ? b.ncnt[s] : 0;
     const unsigned below = (1u << lane) - 1u;
     int nr = 0;   // rigid entries collected
     // the entry of the next round is fetched one round ahead
@@ -2001,49 +2034,83 @@ __global__ void __launch_bounds__(RB) k_force_rigid(Bufs b, int velver)
         if (rig) rl[nr + __popc(rb & below)] = e;
         nr += __popc(rb);
     }
-    __syncwarp();
-    // rigid neighbours: DEM contact with its history slot in list order, or
-    // lubrication
-    int base = 0;
-    for (int q0 = 0; q0 < nr; q0 += 32) {
-        const int q = q0 + lane;
-        bool contact = false;
-        int partner = 0;
-        double dn[3] = { 0.0, 0.0, 0.0 };
-        if (q < nr) {
-            const int j = (int)(rl[q] & ~NB_FAR);
+    if (lane == 0) s_nr[warp] = nr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_pre[0] = 0;
+        for (int w = 0; w < RPB; ++w) s_pre[w + 1] = s_pre[w] + s_nr[w];
+    }
+    __syncthreads();
+    // the pooled rigid pairs (sphere w's entries at [s_pre[w], s_pre[w+1])),
+    // RB at a time: DEM contact, or lubrication
+    const int total = s_pre[RPB];
+    double mine = 0.0;   // lane c < 9 of a live warp: component c of F_dem, T_dem, F_lub
+    int base = 0;        // history slots used so far (the same on every lane)
+    for (int c0 = 0; c0 < total; c0 += RB) {
+        const int p = c0 + threadIdx.x;
+        if (p < total) {
+            int ws = 0;
+            while (ws + 1 < RPB && s_pre[ws + 1] <= p) ++ws;
+            const uint32_t e = lists[(size_t)ws * b.cap + (p - s_pre[ws])];
+            const Inst &Iw = b.inst[s_inst[ws]];
+            const double xs[3] = { s_x[ws][0], s_x[ws][1], s_x[ws][2] };
+            const double Rs = s_R[ws];
+            RigidPairRes &o = pres[threadIdx.x];
+            for (int a = 0; a < 3; ++a) {
+                o.F[a] = 0.0;
+                o.T[a] = 0.0;
+                o.L[a] = 0.0;
+                o.dn[a] = 0.0;
+            }
+            o.partner = -1;
+            const int j = (int)(e & ~NB_FAR);
             const int gj = b.perm[j];
             const double xj[3] = { b.x[3 * gj], b.x[3 * gj + 1], b.x[3 * gj + 2] };
             double rv[3];
-            const double r2 = exact_disp(xi, xj, I, rv);
+            const double r2 = exact_disp(xs, xj, Iw, rv);
             const double L = sqrt(r2);
-            const double vij[3] = { vi[0] - b.v[3 * gj], vi[1] - b.v[3 * gj + 1], vi[2] - b.v[3 * gj + 2] };
+            const double vij[3] = { s_v[ws][0] - b.v[3 * gj], s_v[ws][1] - b.v[3 * gj + 1],
+                                    s_v[ws][2] - b.v[3 * gj + 2] };
             const double Rj = b.R[gj];
-            const double dsum = Ri + Rj;
+            const double dsum = Rs + Rj;
             if (L < dsum) {
                 const double nn[3] = { rv[0] / L, rv[1] / L, rv[2] / L };
                 double wsR[3];
-                for (int a = 0; a < 3; ++a) wsR[a] = Ri * wi[a] + Rj * b.w[3 * gj + a];
+                for (int a = 0; a < 3; ++a) wsR[a] = Rs * s_w[ws][a] + Rj * b.w[3 * gj + a];
                 double kn, kt, cn, ct;
-                dem_coeffs(I, Ri, Rj, mi, b.m[gj], kn, kt, cn, ct);
-                dem_pair(b, I, r, gj, nn, L - dsum, vij, wsR, Ri, kn, kt, cn, ct, acc + 6, acc + 9, dn);
-                contact = true;
-                partner = gj;
-            } else if (r2 < I.rc2) {
+                dem_coeffs(Iw, Rs, Rj, s_m[ws], b.m[gj], kn, kt, cn, ct);
+                dem_pair(b, Iw, s_r[ws], gj, nn, L - dsum, vij, wsR, Rs, kn, kt, cn, ct, o.F, o.T, o.dn);
+                o.partner = gj;
+            } else if (r2 < Iw.rc2) {
                 double gap = L - dsum;
-                const double gmin = I.lub_gap_min * dsum;
+                const double gmin = Iw.lub_gap_min * dsum;
                 if (gap < gmin) gap = gmin;
-                const double c = 3.0 * PI * I.eta * dsum * dsum / (8.0 * gap);
-                for (int a = 0; a < 3; ++a) acc[12 + a] += c * (-vij[a]);
+                const double c = 3.0 * PI * Iw.eta * dsum * dsum / (8.0 * gap);
+                for (int a = 0; a < 3; ++a) o.L[a] = c * (-vij[a]);
             }
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, contact);
-        if (commit && contact) hist_put(b, r, base + __popc(bal & below), partner, dn);
-        base += __popc(bal);
+        __syncthreads();
+        // each sphere adds its own pairs of this chunk in list order
+        if (live) {
+            const int lo = max(s_pre[warp], c0) - c0, hi = min(s_pre[warp + 1], c0 + RB) - c0;
+            for (int t = lo; t < hi; ++t) {
+                const RigidPairRes &o = pres[t];
+                if (lane < 9) mine += lane < 3 ? o.F[lane] : (lane < 6 ? o.T[lane - 3] : o.L[lane - 6]);
+                if (o.partner >= 0) {
+                    if (lane == 0 && commit) hist_put(b, r, base, o.partner, o.dn);
+                    ++base;
+                }
+            }
+        }
+        __syncthreads();
     }
+    if (!live) return;   // past the block's last barrier
     acc[0] = f0; acc[1] = f1; acc[2] = f2;
     acc[3] = t0; acc[4] = t1; acc[5] = t2;
-    warp_sum_all(acc);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) acc[a] = warp_sum(acc[a]);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[6 + c] = __shfl_sync(0xffffffffu, mine, c);
     if (lane != 0) return;
     // contact with the planes bounding the domain on wall axes
     for (int a = 0; a < 3; ++a) {
@@ -2153,6 +2220,12 @@ static size_t stream_smem_bytes(int block) { return (size_t)(block / 32) * sizeo
 
 void init_pair_kernels()
 {
+    // the sphere kernel's rigid lists and pooled-pair results at the largest
+    // list capacity
+    cudaFuncSetAttribute(k_force_rigid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rigid_smem_bytes(SDPD_MAX_NEIGHBORS));
+    cudaFuncSetAttribute(k_force_rigid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rigid_smem_bytes(SDPD_MAX_NEIGHBORS));
     // the pair-stream kernels' shared memory at the largest block (256)
     cudaFuncSetAttribute(k_force_stream<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stream_smem_bytes<float>(256));
@@ -2249,7 +2322,7 @@ void launch_forces(const Bufs &b, int precision, int velver, int newton3, cudaSt
     }
     if (b.nrigid) {
         const unsigned g = nblk(b.nrigid, RPB);
-        const size_t smem = (size_t)RPB * b.cap * sizeof(uint32_t);
+        const size_t smem = rigid_smem_bytes(b.cap);
         if (precision == SDPD_PREC_SPLIT) k_force_rigid<float><<<g, RB, smem, st>>>(b, velver);
         else k_force_rigid<double><<<g, RB, smem, st>>>(b, velver);
         if (velver == 2) k_hist_copy<<<nblk(b.nrigid, 64), 64, 0, st>>>(b);
