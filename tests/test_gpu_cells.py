@@ -3,7 +3,8 @@
 oracle: the pairs within h exactly, forces per particle type within the
 parity tolerances for every force variant, contacts of dry granular matter,
 trajectories equal to full-size cells up to summation order, capacity
-overflow reported, the largest list capacity, a crowded cell."""
+overflow reported, the largest list capacity, a crowded cell, and spheres
+crowded enough that the sphere kernel pools its DEM pairs over several rounds."""
 import numpy as np
 import pytest
 
@@ -190,6 +191,29 @@ def test_half_cells_crowded_cell(precision):
     assert pair_set(sim.pairs()) == pair_set(orc.pairs())
     orc.evaluate(1)
     assert rel_l2(sim.state()["F"], orc.state()["F"]) < TOL_FORCE[precision]
+    sim.close()
+
+
+@pytest.mark.parametrize("cells", [1, 2])
+def test_crowded_spheres_pool_over_several_rounds(cells):
+    # spheres only, about 71 sphere neighbours each (kernel radius 2.5
+    # spacings), many in contact: a block's four spheres pool about 280 sphere
+    # pairs, so the pooled DEM and lubrication run over several rounds and the
+    # history slots continue across them
+    c = cases.tiny_box(n=8, r_c_dx=2.5, jitter=0.15, seed=7)
+    n = len(c["x"])
+    c = dict(c, type=np.ones(n, dtype=c["type"].dtype), radius=np.full(n, 0.55),
+             mass=np.full(n, c["params"]["rho0"] * 4.0 / 3.0 * np.pi * 0.55 ** 3 * 2.7))
+    c["v"] = np.random.default_rng(3).normal(0, 0.05, (n, 3))
+    sim = B.Sim(c, precision=B.SDPD_PREC_FP64)
+    sim.set_cell_factor(cells)
+    sim.step(6)
+    o = oracle.OracleSim(c)
+    o.run(6)
+    g, so = sim.state(density=False), o.state()
+    assert rel_l2(g["v"], so["v"]) < 1e-9
+    scale = np.linalg.norm(so["v"]) / 0.55
+    assert np.linalg.norm(g["w"] - so["w"]) <= 1e-9 * scale
     sim.close()
 
 
