@@ -63,8 +63,10 @@ FP32_PEAK_TF = 152 * 128 * 2 * 2070e6 / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    # the viscometers start from rest; by about step 25 the lists need a
+    # rebuild every few steps, so the default window runs past that point
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "split"],
@@ -200,13 +202,30 @@ def time_graph_path(case, precision, args, local, stream, flush, ws):
         dist.barrier()
     torch.cuda.synchronize()
     ms = []
+    builds0 = sim.build_count()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             ms.append(_timed(stream, lambda: sim.step(1, stream), flush))
+    builds = sim.build_count() - builds0   # list builds the skin triggered inside the timed steps
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     kernels = sim.graph_kernels()
+    # end-to-end through the C ABI with host buffers, right after the timed
+    # steps (the loops below move the state in ways a run would not): upload
+    # the step's state from pinned memory, run the step, read the result back
+    N = sim.N
+    hx = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
+    hv = torch.empty_like(hx)
+    hw = torch.empty_like(hx)
+    sim.download_state(hx, hv, hw, stream=stream)
+    torch.cuda.synchronize()
+
+    def e2e_step():
+        sim.upload_state(hx, hv, hw, stream=stream)
+        sim.step(1, stream)
+        sim.download_state(hx, hv, hw, stream=stream)
+    e2e_ms = [_timed(stream, e2e_step, flush) for _ in range(max(3, args.steps // 2))]
     # dominant kernel (force pass, velver 1) timed alone on the stream it is
     # launched on, L2 flushed before each launch
     fms = []
@@ -227,25 +246,12 @@ def time_graph_path(case, precision, args, local, stream, flush, ws):
     torch.cuda.synchronize()
     # the HBM-bound update kernel alone (velocity Verlet, velver 1)
     ims = [_timed(stream, lambda: sim.integrate(1, stream), flush) for _ in range(5)]
-    # end-to-end through the C ABI with host buffers: upload the step's state
-    # from pinned memory, run the step, read the result back
-    N = sim.N
-    hx = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
-    hv = torch.empty_like(hx)
-    hw = torch.empty_like(hx)
-    sim.download_state(hx, hv, hw, stream=stream)
-    torch.cuda.synchronize()
-
-    def e2e_step():
-        sim.upload_state(hx, hv, hw, stream=stream)
-        sim.step(1, stream)
-        sim.download_state(hx, hv, hw, stream=stream)
-    e2e_ms = [_timed(stream, e2e_step, flush) for _ in range(max(3, args.steps // 2))]
     mobile = int(sum(int(np.sum(c["type"] <= 1)) for c in sim.cases))
     out = dict(pairs=pairs, ms=float(sum(ms)), per_step=ms, kernels=kernels,
                force_ms=float(np.median(fms)), density_ms=float(np.median(dms)),
                build_ms=float(np.median(bms)),
-               e2e_ms=float(np.mean(e2e_ms)), integrate_ms=float(np.median(ims)), mobile=mobile,
+               e2e_ms=float(np.mean(e2e_ms)), e2e_per_step=[float(t) for t in e2e_ms], builds=builds,
+               integrate_ms=float(np.median(ims)), mobile=mobile,
                setting=setting, e2e_bytes=3 * N * 3 * 8, clocks=clk.summary(), N=N,
                instances=len(sim.cases))
     sim.close()
@@ -623,11 +629,12 @@ def main():
                          "pair_evals_per_s": pairs / (main_r["density_ms"] / 1e3),
                          "note": "density + EOS (+ filter or reinitialisation where the workload "
                                  "has them) after a list build, L2 flushed, events on the stream"},
-        "list_build": {"ms_per_build": main_r["build_ms"],
+        "list_build": {"ms_per_build": main_r["build_ms"], "builds_in_timed_steps": main_r["builds"],
                        "note": "one forced build (cell sort, mirrors, neighbour lists, reverse index "
                                "where the force variant needs it), L2 flushed, events on the stream; "
                                "inside the timed steps builds run only when the skin is exceeded"},
-        "step_ms": {"min": float(np.min(main_r["per_step"])), "median": float(np.median(main_r["per_step"])),
+        "step_ms": {"samples": [round(float(t), 3) for t in main_r["per_step"]],
+                    "min": float(np.min(main_r["per_step"])), "median": float(np.median(main_r["per_step"])),
                     "max": float(np.max(main_r["per_step"]))},
         "gpu_launches": main_r["kernels"] * args.steps,
         "clocks": main_r["clocks"],
@@ -655,7 +662,8 @@ def main():
                        "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json); algorithmic bytes: "
                                "read x, v, w, F, N, m, I and write x, v, w of each mobile particle"},
         "e2e": {"value": pairs * 2 / (main_r["e2e_ms"] / 1e3) * ws, "unit": UNIT,
-                "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"]},
+                "h2d_bytes_per_step": main_r["e2e_bytes"], "d2h_bytes_per_step": main_r["e2e_bytes"],
+                "ms_per_step": main_r["e2e_ms"], "ms_samples": main_r["e2e_per_step"]},
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
     if other_r is not None and split:

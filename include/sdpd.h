@@ -130,6 +130,11 @@ sdpd_status sdpd_download_state(sdpd_ctx *ctx, double *x, double *v, double *w, 
 sdpd_status sdpd_set_step(sdpd_ctx *ctx, long long step);
 sdpd_status sdpd_get_step(sdpd_ctx *ctx, long long *step);
 
+/* Number of neighbour-list builds the context has run (forced ones and
+ * those the Verlet skin triggered inside the steps), a measurement aid.
+ * Synchronous.  SDPD_E_INVALID for a NULL argument. */
+sdpd_status sdpd_build_count(sdpd_ctx *ctx, long long *builds);
+
 /* compute_neighbor_list (Algorithm 1; Section 3.2): background grid of cells
  * at least max(h, largest sphere diameter) wide, counting sort of the
  * particles into Morton-ranked cells (deterministic order within a cell), the

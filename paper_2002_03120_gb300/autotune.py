@@ -9,9 +9,11 @@ the choice in a JSON file keyed by GPU name, precision and size class (total
 particles rounded to a power of two, number of instances), so later contexts
 of the same class reuse it without measuring again.
 
-The measurement uses CUDA events on one stream after warm-up steps; the
-choice never changes results beyond summation order (all settings evaluate
-the same pairs exactly).
+The measurement uses CUDA events on one stream after warm-up steps, with one
+forced list build in each measured window of `steps` steps (runs rebuild the
+lists every few steps once the particles move, and the settings differ in its
+cost); the choice never changes results beyond summation order (all settings
+evaluate the same pairs exactly).
 """
 from __future__ import annotations
 
@@ -151,6 +153,9 @@ def tune(cases, precision=B.SDPD_PREC_SPLIT, steps=10, warmup=3, cache_path=DEFA
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
+            # one list build per measured window: a run rebuilds every few
+            # steps once the particles move, and the settings differ in its cost
+            sim.build_cells(stream)
             sim.step(steps, stream)
             b.record(stream)
             b.synchronize()

@@ -74,7 +74,7 @@ EXPORTS = ["sdpd_init", "sdpd_destroy", "sdpd_set_particles", "sdpd_upload_state
            "sdpd_compute_density", "sdpd_couple_drag", "sdpd_compute_forces", "sdpd_integrate",
            "sdpd_step", "sdpd_viscosity_probe", "sdpd_get_state", "sdpd_get_drag",
            "sdpd_get_pairs", "sdpd_count_pairs", "sdpd_diagnostics", "sdpd_graph_kernels",
-           "sdpd_set_force_mode", "sdpd_set_noise_cache", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_set_threads_per_particle", "sdpd_set_cell_factor", "sdpd_density_noalloc",
+           "sdpd_set_force_mode", "sdpd_set_noise_cache", "sdpd_set_skin", "sdpd_set_block_size", "sdpd_set_threads_per_particle", "sdpd_set_cell_factor", "sdpd_build_count", "sdpd_density_noalloc",
            "sdpd_check",
            "sdpd_last_error", "sdpd_noise_normals", "sdpd_philox4x32_10", "sdpd_alu_peaks", "sdpd_viscosity_fit", "sdpd_checkpoint_size", "sdpd_checkpoint", "sdpd_restore", "mlp_init", "mlp_destroy", "mlp_param_count", "mlp_set_params",
            "mlp_get_params", "mlp_gradients", "mlp_train_step", "mlp_infer", "mlp_check"]
@@ -135,6 +135,7 @@ def load(build_if_missing: bool = True):
         "sdpd_philox4x32_10": (st, [C.c_longlong, vp, vp, vp]),
         "sdpd_set_threads_per_particle": (st, [vp, C.c_int]),
         "sdpd_set_cell_factor": (st, [vp, C.c_int]),
+        "sdpd_build_count": (st, [vp, C.POINTER(C.c_longlong)]),
         "sdpd_alu_peaks": (st, [vp]),
         "mlp_init": (st, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.POINTER(vp)]),
         "mlp_destroy": (None, [vp]),
@@ -275,6 +276,12 @@ class Sim:
     def download_state(self, x=None, v=None, w=None, F=None, N=None, stream=None):
         _check(load().sdpd_download_state(self._h, _ptr(x), _ptr(v), _ptr(w), _ptr(F), _ptr(N),
                                           _stream(stream)))
+
+    def build_count(self) -> int:
+        """Neighbour-list builds run so far (forced and skin-triggered)."""
+        n = C.c_longlong()
+        _check(load().sdpd_build_count(self._h, C.byref(n)))
+        return n.value
 
     @property
     def step_count(self) -> int:

@@ -796,6 +796,16 @@ sdpd_status sdpd_get_step(sdpd_ctx *c, long long *step)
     return SDPD_OK;
 }
 
+sdpd_status sdpd_build_count(sdpd_ctx *c, long long *builds)
+{
+    if (!c || !builds) return fail(SDPD_E_INVALID, "NULL argument");
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned e = 0;
+    CUDA_TRY(cudaMemcpy(&e, c->b.list_epoch, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *builds = (long long)e;
+    return SDPD_OK;
+}
+
 sdpd_status sdpd_build_cells(sdpd_ctx *c, void *stream)
 {
     if (!c) return fail(SDPD_E_INVALID, "NULL context");
