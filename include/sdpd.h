@@ -235,7 +235,9 @@ sdpd_status sdpd_diagnostics(sdpd_ctx *ctx, int inst, double out[16]);
  * and the partner gathers it through the reverse index; 4 and 1 give the
  * same bits); newton3 = 5 is the direct pass with only the list index and
  * the partner's position fetched ahead, which needs fewer registers and runs
- * more warps per SM (FP32 pairs; FP64 runs 0; the same bits as 0).  All give
+ * more warps per SM, its other records coming at the first evaluation through
+ * an asynchronous shared-memory ring (FP32 pairs; FP64 runs 0; the same bits
+ * as 0).  All give
  * the same forces up to summation order.
  * Invalidates the current neighbour build and graph.  Synchronous. */
 sdpd_status sdpd_set_force_mode(sdpd_ctx *ctx, int newton3);
