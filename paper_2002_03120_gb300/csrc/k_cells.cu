@@ -370,13 +370,13 @@ constexpr int NG_MAX_WARPS = 4;
 constexpr int NG_OFF = 256;    // largest neighbour cell of the 16-bit entries
 
 struct NgShared {
-    int pre[NG_TAB + 1];       // candidates before each neighbour cell (flattened index)
-    int js[NG_TAB];            // first slot of each neighbour cell
-    int code[NG_TAB];          // its offset code (ox+2) + 5 (oy+2) + 25 (oz+2)
     float4 sa[NG_STAGE];       // staged candidates: record,
     int sj[NG_STAGE];          //   slot,
-    int sq[NG_STAGE];          //   neighbour cell << 8 | offset in it,
     float sr[NG_STAGE];        //   radius where it can be a contact partner, else 0
+    int sq[NG_STAGE];          //   neighbour cell << 8 | offset in it
+    int pre[NG_TAB + 1];       // candidates before each neighbour cell (flattened index)
+    int js[NG_TAB];            // first slot of each neighbour cell
+    uint8_t code[NG_TAB];      // its offset code (ox+2) + 5 (oy+2) + 25 (oz+2) < 125
     float4 ai[NG_G];           // the group's records,
     float ri[NG_G];            //   rigid radii
 };
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(NG_MAX_WARPS * 32) k_neighbors_grp(Bufs b, con
         if (code >= 0) {
             S.pre[q] = total + v - cnt;
             S.js[q] = js;
-            S.code[q] = code & 127;
+            S.code[q] = (uint8_t)(code & 127);
         }
         total += __shfl_sync(FULL, v, 31);
         const unsigned vm = __ballot_sync(FULL, code >= 0);
