@@ -76,14 +76,18 @@ def _sampled(setting, candidates, precision):
     when asked for, at the two larger blocks and the two middle skins, the
     three-block variant for FP32 pairs only.  Half-size cells: the Newton-3,
     direct and lean direct passes at the default block and the three smaller
-    skins."""
+    skins, and the direct pass with several lanes per particle at the default
+    block and skin."""
     mode, skin, block = setting["newton3"], setting["skin"], setting["block"]
     skins = candidates["skin"]
     if setting.get("cells", 1) != 1:
-        # half-size cells: one lane per particle, the default block, the
-        # three smaller skins; Newton 3, direct and lean direct (FP32)
-        if setting.get("tpp", 1) != 1 or block != 128 or skin not in skins[:3]:
+        # half-size cells: the default block, the three smaller skins; Newton
+        # 3, direct and lean direct (FP32) with one lane per particle, and
+        # the direct pass with several lanes at the default skin
+        if block != 128 or skin not in skins[:3]:
             return False
+        if setting.get("tpp", 1) != 1:
+            return mode == 0 and skin == skins[min(1, len(skins) - 1)]
         return mode in (0, 1) or (mode == 5 and precision != B.SDPD_PREC_FP64)
     if setting.get("tpp", 1) != 1:
         # several lanes per particle: the direct pass at the default block

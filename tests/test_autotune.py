@@ -22,11 +22,13 @@ def test_search_picks_fastest_and_skips_nothing_required():
     assert best == {"newton3": 1, "skin": 0.12, "block": 128, "tpp": 1, "cells": 1}
     # several lanes per particle only for the direct pass, default block and skin
     assert {(r["newton3"], r["block"], r["skin"]) for r in table if r["tpp"] != 1} == {(0, 128, 0.03)}
-    # half-size cells: one lane per particle, default block, the smaller skins
+    # half-size cells: default block, the smaller skins; several lanes per
+    # particle only for the direct pass at the default skin
     half = [r for r in table if r["cells"] == 2]
-    assert {(r["tpp"], r["block"]) for r in half} == {(1, 128)}
+    assert {r["block"] for r in half} == {128}
     assert {r["skin"] for r in half} == {0.0, 0.03, 0.06}
     assert {r["newton3"] for r in half} == {0, 1, 5}
+    assert {(r["newton3"], r["skin"]) for r in half if r["tpp"] != 1} == {(0, 0.03)}
     assert min(r["ms"] for r in table) == pytest.approx(fake(best))
     assert {r["newton3"] for r in table} == {0, 1, 5}
     # asked for, the pair stream is sampled at the two larger blocks and

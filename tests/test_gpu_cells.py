@@ -84,6 +84,23 @@ def test_half_cells_forces_per_type(name, precision, mode):
         sim.close()
 
 
+@pytest.mark.parametrize("tpp", [2, 4])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_half_cells_lanes_per_particle(precision, tpp):
+    # the direct pass with several lanes per particle on half-size cells
+    case = _moving(CASES["sediment_small"], 5)
+    sim = _half(case, precision)
+    sim.set_force_mode(0)
+    sim.set_threads_per_particle(tpp)
+    sim.step_count = 2
+    sim.evaluate(1)
+    orc = oracle.OracleSim(case)
+    orc.step = 2
+    orc.evaluate(1)
+    check_per_type(sim.state(), orc.state(), case["type"], TOL_FORCE[precision])
+    sim.close()
+
+
 def test_half_cells_dry_granular_contacts():
     # spheres only, some touching: contact-range entries (beyond h) and
     # their tangential history must be listed exactly as with full cells
